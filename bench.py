@@ -1,0 +1,269 @@
+"""Benchmark of the purified quantics-MPS Lindblad step on GB300.
+
+Workload (the large single cat mode): one bosonic mode of N = 512 Fock levels
+(R = 9 quantics sites), L1 = sqrt(k2)(a^2 - alpha^2) with alpha^2 = 32,
+L2 = sqrt(k1) a with k1/k2 = 1e-3, Zeno drive H = 0.1 (a + a^dag), dt = 5e-4,
+bond cap chi <= 64, purification cap chi_mu <= 16, cutoff 1e-12, from vacuum.
+A "step" is one first-order Kraus step (apply + stack + recompress + purify +
+renormalise).  W warm-up steps are run first, then K steps are timed with CUDA
+events on the library's stream, L2 flushed (256 MiB write) between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 dense oracle on
+the host cores instead (bounded sample).  Under torchrun each rank steps its own
+replica (no collective); value = steps of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Lindblad steps/s at <=1e-6 obs. error vs plain FP64 form; batched p50/p99 latency"
+WORKLOAD = "cat_r9"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def run_reference(args):
+    """FP64 dense oracle of the same workload on the host cores (bounded sample)."""
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle import dense as D
+    from oracle import systems as OS
+    from paper_2605_27515_gb300 import inputs
+
+    cfg = inputs.config(WORKLOAD)
+    ds = OS.cat(cfg)
+    rho = ds.rho0()
+    for _ in range(max(1, args.warmup)):
+        rho = D.kraus_step(rho, ds.H0, ds.Ls, cfg["dt"])
+    t0 = time.perf_counter()
+    n = 0
+    budget = 20.0
+    while n < args.steps or (time.perf_counter() - t0) < 0.1:
+        rho = D.kraus_step(rho, ds.H0, ds.Ls, cfg["dt"])
+        n += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    v = n / dt
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": world,
+            "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * dt / n, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": 512, "alpha2": 32.0, "dt": cfg["dt"], "form": "dense rho"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} dense FP64 Kraus steps of the N=512 cat after {args.warmup} warm-up steps"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """The dense oracle on a bounded sample of the same workload (rank 0, N=1)."""
+    from oracle import dense as D
+    from oracle import systems as OS
+    from paper_2605_27515_gb300 import inputs
+
+    cfg = inputs.config(WORKLOAD)
+    ds = OS.cat(cfg)
+    rho = ds.rho0()
+    rho = D.kraus_step(rho, ds.H0, ds.Ls, cfg["dt"])
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < 10.0 and n < 200:
+        rho = D.kraus_step(rho, ds.H0, ds.Ls, cfg["dt"])
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} dense FP64 Kraus steps of the N=512 cat (about {dt:.0f} s of host time)"}
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2605_27515_gb300 import inputs, qlb, systems
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local
+    torch.cuda.set_device(dev)
+    cfg = inputs.config(WORKLOAD)
+    ctx = qlb.Ctx(device=dev, precision=args.precision, tol=cfg["tol"], chi_max=cfg["chi_max"],
+                  chi_mu_max=cfg["chi_mu_max"], stream_ordered=1)
+    b = systems.build(ctx, cfg)
+    st = b.sys.state(b.init)
+    stream = torch.cuda.ExternalStream(ctx.stream(), device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    dt = cfg["dt"]
+    status = st.step(dt, args.warmup)
+    ctx.synchronize()
+    bonds_before = st.bond_dims()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                evs[k][0].record(stream)
+                status = max(status, st.step(dt, 1))
+                evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    ms = [a.elapsed_time(bb) for a, bb in evs]
+    total_ms = float(sum(ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    bonds_after = st.bond_dims()
+    value = world * args.steps / (total_ms / 1e3)
+
+    # kernel-class breakdown of the same steps (events around every launch)
+    ctx.profile_enable(True)
+    ctx.profile_reset()
+    st.step(dt, args.steps)
+    ctx.synchronize()
+    prof = {qlb.K_NAMES[k]: ctx.profile_read(k) for k in range(qlb.K_COUNT)}
+    ctx.profile_enable(False)
+    launches_per_step = sum(p["launches"] for p in prof.values()) / args.steps
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    dp = prof[dom]
+    peaks = _peaks()
+    fp64_peak = args.fp64_peak_tflops
+    achieved = dp["flops"] / (dp["ms"] / 1e3) / 1e12 if dp["ms"] > 0 else 0.0
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; no FP64 figure in the measured peaks)",
+                "launches": dp["launches"], "ms_per_launch": dp["ms"] / max(1, dp["launches"]),
+                "flops_per_launch": dp["flops"] / max(1, dp["launches"])}
+
+    # end to end through the public API: host vectors in, K steps, observables out
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st2 = b.sys.state(b.init)
+    st2.step(dt, args.warmup + args.steps)
+    n_obs = st2.expectation(b.observables["n"])
+    p_obs = st2.expectation(b.observables["parity"])
+    e2e_s = time.perf_counter() - t0
+    e2e_steps = args.warmup + args.steps
+    h2d = 16 * 512
+    d2h = 2 * 16
+    st2.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "mixed",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": 512, "R": 9, "alpha2": 32.0, "eps_z": 0.1, "dt": dt, "chi_max": 64,
+                   "chi_mu_max": 16, "tol": 1e-12, "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single", "bonds_before": bonds_before,
+                   "bonds_after": bonds_after, "step_status": int(status)},
+        "roofline": roofline,
+        "kernel_classes_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+        "e2e": {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d / e2e_steps,
+                "d2h_bytes_per_step": d2h / e2e_steps, "observables": [n_obs.real, p_obs.real]},
+        "gpu_launches": int(round(launches_per_step * args.steps)),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    st.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

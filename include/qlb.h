@@ -1,0 +1,233 @@
+/*
+ * qlb.h -- C-ABI of the GB300 purified quantics-MPS Lindblad stepper (libqlb.so).
+ *
+ * What the library computes (Moulinas & Waintal, "A multilevel tensor network
+ * compression technique for simulating Lindblad dynamics in superconducting
+ * circuits"):
+ *   * the Lindblad equation, Eq. 1, with hbar = 1, for a few bosonic modes;
+ *   * the density matrix is kept as a global purification rho = Psi Psi^dag
+ *     (Sec. IV.A) whose Psi is a matrix product state over the quantics sites of
+ *     all modes (Sec. IV.B-C): mode m of N_m = 2^R_m Fock levels is split into
+ *     R_m binary sites, sigma_1 (most significant bit) first (Sec. II.A);
+ *   * one step is the first-order Kraus map K = U + h L of Sec. V.B with
+ *     U_1 = 1 - i h H_eff, H_eff = H - (i/2) sum_k L_k^dag L_k, the jump
+ *     branches sqrt(h) L_k stacked on the purification index (matrix addition,
+ *     Sec. V.A), every bond recompressed, the purification rank truncated
+ *     (Sec. IV.A) and rho renormalised to unit trace (Sec. V.B, last paragraph).
+ *
+ * Conventions common to every call:
+ *   * Complex numbers are passed as interleaved (re, im) doubles (the layout of
+ *     C99 double _Complex and numpy complex128).
+ *   * Dense per-mode matrices are N_m x N_m, row-major, complex128.
+ *   * Inputs are copied during the call; the caller keeps ownership of every
+ *     buffer it passes.  Every handle is created and destroyed by the caller;
+ *     destroying a system invalidates the ops and states made from it.
+ *   * All device memory is owned by the library; state tensors stay resident on
+ *     the GPU.  Host pointers are plain host memory (pageable or pinned).
+ *   * Every call returns a qlb_status: 0 on success, > 0 a warning (the call
+ *     did its work), < 0 an error (the call did nothing that the caller can
+ *     observe, except where a call says otherwise).  No call aborts the process.
+ *     qlb_last_error() returns a thread-local message for the last failing call.
+ *   * Calls are synchronous unless qlb_options.stream_ordered is set, in which
+ *     case qlb_step returns after enqueueing work on the context's stream.
+ *   * A context serialises its work on one CUDA stream; handles of one context
+ *     must not be used from several host threads at once.
+ */
+#ifndef QLB_H
+#define QLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t qlb_status;
+
+#define QLB_OK 0
+#define QLB_WUNSTABLE 1    /* warning: the explicit U_1 = 1 - i h H_eff has a spectral
+                              bound above 1 at this dt (Sec. III.A stiffness remark) */
+#define QLB_EINVAL (-1)     /* bad argument (null handle, size, mode index ...) */
+#define QLB_ENOMEM (-2)     /* device allocation failed or the HBM budget is exceeded */
+#define QLB_ENOTCONV (-3)   /* a Jacobi eigen/SVD solve hit its sweep limit */
+#define QLB_ETIMEOUT (-4)   /* a bounded device wait gave up */
+#define QLB_ENONFINITE (-5) /* NaN/Inf met in the state or a trace */
+#define QLB_EDEVICE (-6)    /* CUDA error or no usable device */
+#define QLB_ESTATE (-7)     /* handle not ready for this call (e.g. no Hamiltonian) */
+
+typedef struct qlb_ctx qlb_ctx;
+typedef struct qlb_system qlb_system;
+typedef struct qlb_op qlb_op;
+typedef struct qlb_state qlb_state;
+
+/* Arithmetic of the step. */
+#define QLB_PREC_F64 0   /* every operation in FP64 (the parity form) */
+#define QLB_PREC_MIXED 1 /* contractions and Gram matrices in FP32 split precision,
+                            truncation decisions and renormalisation in FP64 */
+
+typedef struct {
+  int device;            /* CUDA device ordinal */
+  int precision;         /* QLB_PREC_* */
+  double tol;            /* relative discarded-weight cutoff: keep the smallest k with
+                            sum_{i>=k} s_i^2 <= tol * sum_i s_i^2 (default 1e-12) */
+  int chi_max;           /* cap on every inter-site bond (default 64) */
+  int chi_mu_max;        /* cap on the purification rank chi_mu (default 16) */
+  double zip_tol_factor; /* the on-the-fly truncation inside the MPO application uses
+                            tol * zip_tol_factor (default 1e-2) */
+  double degeneracy_gap; /* singular values within this relative gap are one cluster and
+                            are never split by a cut (default 1e-10) */
+  int max_sweeps;        /* Jacobi sweep limit before QLB_ENOTCONV (default 40) */
+  size_t hbm_budget;     /* bytes of device memory the context may hold; 0 = no limit */
+  int stream_ordered;    /* 1: qlb_step only enqueues; 0 (default): it synchronises */
+} qlb_options;
+
+/* Fills *opt with the defaults listed above. */
+void qlb_default_options(qlb_options* opt);
+
+/* Creates a context on opt->device (opt may be NULL for defaults). */
+qlb_status qlb_create(const qlb_options* opt, qlb_ctx** out);
+void qlb_destroy(qlb_ctx* ctx);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* qlb_last_error(void);
+
+/* The cudaStream_t the context launches on (for callers that time with events). */
+qlb_status qlb_ctx_stream(qlb_ctx* ctx, void** stream);
+/* Waits for all work of the context. */
+qlb_status qlb_synchronize(qlb_ctx* ctx);
+/* Device bytes currently held by the context. */
+qlb_status qlb_ctx_memory(qlb_ctx* ctx, size_t* bytes);
+
+/* ------------------------------------------------------------------ systems */
+
+/* A system of n_modes bosonic modes; mode m has N_m = 2^R[m] levels (1 <= R[m] <= 12,
+ * sum R[m] <= 64).  Sec. II.A (quantics encoding), Sec. IV.C (one quantics chain
+ * per mode, modes joined by compressed bonds). */
+qlb_status qlb_system_create(qlb_ctx* ctx, int n_modes, const int* R, qlb_system** out);
+void qlb_system_destroy(qlb_system* sys);
+
+/* ------------------------------------------------------------------ operators */
+
+/* Built-in single-mode factors (Sec. II.B; Sec. VII for the charge basis). */
+#define QLB_F_ID 0     /* identity */
+#define QLB_F_A 1      /* a: <n|a|n'> = delta_{n+1,n'} sqrt(n'), open at n = 0 */
+#define QLB_F_ADAG 2   /* a^dag, the conjugate transpose of the truncated a */
+#define QLB_F_NUM 3    /* n = diag(0..N-1) */
+#define QLB_F_PARITY 4 /* (-1)^n */
+#define QLB_F_CHARGE 5 /* diag(j - param): charge operator with charge offset param */
+#define QLB_F_COSPHI 6 /* (|j><j+1| + |j+1><j|)/2, open ends (charge-basis cos phi) */
+#define QLB_F_DENSE 7  /* caller's dense N_m x N_m complex128 row-major matrix */
+
+typedef struct {
+  int mode;            /* 0 <= mode < n_modes */
+  int kind;            /* QLB_F_* */
+  int power;           /* factor raised to this power (>= 1; 0 is treated as 1) */
+  double param;        /* QLB_F_CHARGE offset; ignored otherwise */
+  const double* dense; /* QLB_F_DENSE: 2*N_m*N_m doubles; ignored otherwise */
+} qlb_factor;
+
+/* One term: (re + i im) times the ordered product of its factors.  Factors on
+ * the same mode multiply as matrices in the order given (products of the
+ * truncated matrices, Sec. II.B); factors on different modes are tensored. */
+typedef struct {
+  double re, im;
+  const qlb_factor* factors;
+  int n_factors;
+} qlb_term;
+
+/* Builds sum_t term_t as a quantics MPO (Sec. II.B): each term's per-mode dense
+ * matrix is TT-SVD'd on the device into an MPO of R_m sites, the modes are
+ * joined, the terms are summed and the sum is recompressed.  tol is the relative
+ * discarded weight per bond (<= 0 selects 1e-26, i.e. only numerical zeros are
+ * dropped); chi_max caps every MPO bond (<= 0: no cap).  The op keeps its dense
+ * per-mode factors on the device so that L^dag L can be formed exactly. */
+qlb_status qlb_op_build(qlb_system* sys, const qlb_term* terms, int n_terms, double tol, int chi_max,
+                        qlb_op** out);
+void qlb_op_destroy(qlb_op* op);
+/* Bond dimensions D_1..D_{L-1} of the op's MPO (n_out = L-1; cap = size of out). */
+qlb_status qlb_op_bond_dims(const qlb_op* op, int* out, int cap, int* n_out);
+/* Dense matrix of the op's MPO (for small systems, 2^L <= 4096): out holds 2*4^L doubles. */
+qlb_status qlb_op_to_dense(const qlb_op* op, double* out, size_t n_doubles);
+
+/* H(t) = H0 + f(t_n) H1 (Sec. III.A, coefficient form H0 + f(t) H1).  H1 may be NULL.
+ * f_table[n] is f at the left end t_n of the n-th step since the state was made
+ * (first-order step, left endpoint); steps past the end of the table use f = 0.
+ * The ops are referenced, not copied: keep them alive while the system is used. */
+qlb_status qlb_set_hamiltonian(qlb_system* sys, const qlb_op* H0, const qlb_op* H1, const double* f_table,
+                               int64_t n_f);
+/* Adds a Lindblad operator L_k (Eq. 1).  Referenced, not copied. */
+qlb_status qlb_add_jump(qlb_system* sys, const qlb_op* L);
+
+/* ------------------------------------------------------------------ states */
+
+/* Pure separable start, chi_mu = chi_e = 1 (Sec. V, first paragraph): mode_vecs[m]
+ * holds N_m complex128 amplitudes (normalised by the call). */
+qlb_status qlb_state_init_product(qlb_system* sys, const double* const* mode_vecs, qlb_state** out);
+void qlb_state_destroy(qlb_state* st);
+
+/* Sets the truncation parameters used by every later step of this state and
+ * recompresses the state once with them (Sec. V.A compression, Sec. IV.A
+ * purification truncation).  tol <= 0 keeps the current value; chi caps <= 0 keep
+ * theirs.  Caps may not exceed the values the state was allocated for (the
+ * context's chi_max / chi_mu_max at init). */
+qlb_status qlb_truncate(qlb_state* st, double tol, int chi_max, int chi_mu_max);
+
+/* n steps of size dt of the first-order Kraus map (Sec. V.B), each followed by
+ * recompression and renormalisation.  Returns QLB_WUNSTABLE (after doing the
+ * work) if the Gershgorin bound of |U_1| exceeds 1 + 1e-12 at this dt. */
+qlb_status qlb_step(qlb_state* st, double dt, int64_t n);
+
+/* Tr(O rho) for the unit-trace rho of the state; out = (re, im). */
+qlb_status qlb_expectation(qlb_state* st, const qlb_op* O, double* out);
+/* <psi|rho|psi> for the product target psi = (x)_m target_mode_vecs[m] (normalised by the call). */
+qlb_status qlb_fidelity(qlb_state* st, const double* const* target_mode_vecs, double* out);
+/* Tr rho of the stored purification (1 after every step, up to rounding). */
+qlb_status qlb_trace(qlb_state* st, double* out);
+/* Tr rho^2 (Sec. IV.A). */
+qlb_status qlb_purity(qlb_state* st, double* out);
+/* [chi_mu, chi_1, ..., chi_{L-1}] (n_out = L). */
+qlb_status qlb_bond_dims(qlb_state* st, int* out, int cap, int* n_out);
+/* Diagnostics of the last step: out[0] = Tr rho before renormalisation,
+ * out[1] = largest relative discarded weight over the bonds, out[2] = the
+ * Gershgorin bound of |U_1|, out[3] = steps taken since init. */
+qlb_status qlb_step_stats(qlb_state* st, double* out4);
+
+/* Dense purification Psi of a small state (2^L <= 4096) as a 2^L x chi_mu
+ * row-major complex128 matrix, rho = Psi Psi^dag (Sec. IV.A); *chi_mu_out gets
+ * chi_mu.  out must hold 2 * 2^L * chi_mu doubles (n_doubles). */
+qlb_status qlb_state_to_dense(qlb_state* st, double* out, size_t n_doubles, int* chi_mu_out);
+/* Dense matrix of the Kraus operator of branch k (0: U_1 = 1 - i dt H_eff(t_n)
+ * at the state's current step n, k >= 1: sqrt(dt) L_k) exactly as the step
+ * applies it (Sec. V.B), for 2^L <= 2048; out holds 2 * 4^L doubles. */
+qlb_status qlb_kraus_to_dense(qlb_state* st, double dt, int k, double* out, size_t n_doubles);
+
+/* Host copy of the state (checkpoint / preemption): bond dims and site tensors.
+ * qlb_state_export with out == NULL stores the needed size in *n_bytes. */
+qlb_status qlb_state_export(qlb_state* st, void* out, size_t cap, size_t* n_bytes);
+qlb_status qlb_state_import(qlb_state* st, const void* in, size_t n_bytes);
+
+/* ------------------------------------------------------------------ profiling */
+
+/* Kernel classes for qlb_profile_read. */
+#define QLB_K_CONTRACT 0 /* zip-up site contraction (carry x site x MPO) */
+#define QLB_K_GRAM 1     /* Gram matrices of the truncations */
+#define QLB_K_EIG 2      /* Jacobi eigen solves + truncation select */
+#define QLB_K_APPLY 3    /* projections / absorptions after a truncation */
+#define QLB_K_OTHER 4
+#define QLB_K_COUNT 5
+
+/* When enabled, every launch of the step is bracketed by CUDA events on the
+ * context stream and its duration accumulated per kernel class. */
+qlb_status qlb_profile_enable(qlb_ctx* ctx, int on);
+/* Total milliseconds and launches per class since the last reset; flops and
+ * bytes are the algorithmic counts of those launches (device-side shapes). */
+qlb_status qlb_profile_read(qlb_ctx* ctx, int kclass, double* ms, int64_t* launches, double* flops,
+                            double* bytes);
+qlb_status qlb_profile_reset(qlb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QLB_H */

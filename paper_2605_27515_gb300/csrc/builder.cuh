@@ -1,0 +1,42 @@
+// Builder and memory helpers shared by the C-ABI and the step.
+#pragma once
+
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "qlb_objects.cuh"
+
+namespace qlb {
+
+qlb_status dev_alloc(qlb_ctx* ctx, void** p, size_t bytes);
+void dev_free(qlb_ctx* ctx, void* p);
+std::map<void*, std::pair<size_t, qlb_ctx*>>& g_alloc_sizes();
+
+template <typename R>
+cudaError_t launch_gemm(const GemmDesc& g, const int* d_dims, cudaStream_t s, double* prof);
+template <typename R>
+cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof);
+template <typename R>
+size_t eig_smem_bytes(int n_max);
+void init_kernel_attributes();
+
+qlb_status svd_osj(qlb_ctx* ctx, zd* X, int m, int n, double tol, int cap, zd** U, int u_scale, zd** Rr,
+                   int r_unscale, int* k_out, int max_sweeps);
+qlb_status tt_svd(qlb_ctx* ctx, zd* T, int L, int P, double tol, int cap, std::vector<zd*>& cores,
+                  std::vector<int>& D);
+void mpo_clear(qlb_ctx* ctx, Mpo& W);
+qlb_status make_identity_mpo(qlb_ctx* ctx, int R, Mpo& W);
+qlb_status mpo_from_dense(qlb_ctx* ctx, const zd* F, int R, double tol, int cap, Mpo& W);
+void mpo_concat(Mpo& A, Mpo& B);
+qlb_status mpo_scale(qlb_ctx* ctx, Mpo& W, zd c);
+qlb_status mpo_copy(qlb_ctx* ctx, const Mpo& A, Mpo& B);
+qlb_status mpo_stack(qlb_ctx* ctx, const std::vector<const Mpo*>& parts, const std::vector<int>& row_off, int D0,
+                     Mpo& out);
+qlb_status mpo_compress(qlb_ctx* ctx, Mpo& W, double tol, int cap);
+qlb_status make_factor(qlb_ctx* ctx, int N, const qlb_factor& f, zd** out);
+qlb_status dense_mul(qlb_ctx* ctx, const zd* A, int opA, const zd* B, int N, zd** out);
+double dense_inf_norm(qlb_ctx* ctx, const zd* A, int N);
+qlb_status mpo_from_terms(qlb_system* sys, const std::vector<DevTerm>& terms, double tol, int cap, Mpo& out);
+
+}  // namespace qlb

@@ -1,0 +1,134 @@
+// Object model behind the opaque C-ABI handles.
+#pragma once
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "qlb_internal.cuh"
+
+namespace qlb {
+
+// ------------------------------------------------------------------ device buffers
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// ------------------------------------------------------------------ MPOs
+//
+// Builder layout: core i is W[a][p][b] with p = 2*s_out + s_in (the TT-SVD order of
+// the dense matrix).  Step layout: W[s_out][a][s_in][b].
+struct Mpo {
+  int L = 0;
+  std::vector<int> D;      // D[0..L]; D[0] = left boundary (1, or B branches), D[L] = 1
+  std::vector<zd*> core;   // device pointers, builder layout
+  ~Mpo();
+  Mpo() = default;
+  Mpo(const Mpo&) = delete;
+  Mpo& operator=(const Mpo&) = delete;
+  size_t bytes() const;
+};
+
+// A term of an operator, kept on the device: coeff * (x)_m F_m (F_m null = identity).
+struct DevTerm {
+  zd coeff;
+  std::vector<zd*> fac;  // one per mode; owned by the op (shared_ptr-free: freed with the op)
+};
+
+}  // namespace qlb
+
+struct qlb_ctx {
+  qlb_options opt;
+  cudaStream_t stream = nullptr;
+  size_t mem_held = 0;
+  // profiling
+  bool prof_on = false;
+  struct PEv {
+    int kclass;
+    cudaEvent_t a, b;
+  };
+  std::vector<PEv> prof_events;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  double* d_prof = nullptr;  // [QLB_K_COUNT] flops, [QLB_K_COUNT..2*] bytes
+  double prof_ms[QLB_K_COUNT] = {0};
+  long long prof_launch[QLB_K_COUNT] = {0};
+};
+
+struct qlb_system {
+  qlb_ctx* ctx = nullptr;
+  int M = 0;
+  std::vector<int> R;
+  int L = 0;
+  const qlb_op* H0 = nullptr;
+  const qlb_op* H1 = nullptr;
+  std::vector<double> f_table;
+  double* d_f = nullptr;
+  int64_t n_f = 0;
+  std::vector<const qlb_op*> jumps;
+  int version = 0;  // bumped when H or jumps change
+};
+
+struct qlb_op {
+  qlb_system* sys = nullptr;
+  std::vector<qlb::DevTerm> terms;
+  std::vector<qlb::zd*> owned;  // device dense factors owned by this op
+  qlb::Mpo mpo;
+  double inf_norm_bound = 0.0;  // sum_t |c_t| prod_m ||F_m||_inf
+  ~qlb_op();
+};
+
+namespace qlb {
+
+// Stacked Kraus MPO of one step (Sec. V.B): branch k on the left boundary.
+struct Kraus {
+  double dt = -1;
+  int version = -1;
+  int B = 0;            // branches = 1 + number of jumps
+  int L = 0;
+  std::vector<int> D;   // D[0] = B
+  std::vector<zd*> W;   // step layout [s'][a][s][b]
+  bool driven = false;
+  int drive_off = 0;    // first column of the H1 block in bond 1
+  int drive_D1 = 0;     // its width
+  zd* drive_core0 = nullptr;  // H1 core 0, builder layout [1][4][drive_D1], unscaled
+  double unstable_factor = 0;  // h * gamma_bound
+  ~Kraus();
+};
+
+}  // namespace qlb
+
+struct qlb_state {
+  qlb_system* sys = nullptr;
+  int L = 0;
+  int prec = QLB_PREC_F64;
+  // truncation parameters
+  double tol = 1e-12;
+  int chi_max = 64, chi_mu_max = 16;
+  int cap_chi = 64, cap_mu = 16;  // allocation caps
+  // device dims: [0..L] state bonds, [L+1 .. 2L+1] zip-up bonds
+  int* d_dims = nullptr;
+  std::vector<int> cap_state;  // host capacities of state bonds [0..L]
+  // sites (FP64 storage)
+  std::vector<qlb::zd*> site;
+  std::vector<size_t> site_cap;  // elements
+  // scratch
+  qlb::zd *X = nullptr, *Mb = nullptr, *G = nullptr, *Cin = nullptr, *Cout = nullptr;
+  qlb::zd *T1 = nullptr, *T2 = nullptr, *T3 = nullptr, *eigw = nullptr;
+  size_t nX = 0, nM = 0, nG = 0, nC = 0, nT = 0, nEw = 0;
+  double* d_lam = nullptr;
+  double* d_stats = nullptr;  // [0] kept weight (mu), [1] total weight (mu), [2] max disc, [3] scratch
+  int* d_err = nullptr;
+  long long* d_step = nullptr;  // steps taken (drive table index)
+  long long host_steps = 0;
+  // planned step
+  qlb::Kraus kraus;     // stacked Kraus MPO of the current dt
+  qlb::Kraus kraus_id;  // identity (truncate-only passes)
+  int plan_key = 0;     // bumped whenever buffers, caps or the Kraus MPO change
+  cudaGraphExec_t graph = nullptr;
+  int graph_key = -1;
+  std::vector<qlb::DevBuf> extra;  // other owned buffers
+  ~qlb_state();
+};

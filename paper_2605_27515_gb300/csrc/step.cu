@@ -1,0 +1,1019 @@
+// One time step of the purified quantics MPS (Sec. V.B with Sec. V.A and IV.A):
+//
+//   zip-up, left to right, site i = 0..L-1 (MPO.MPS product, Sec. III.A):
+//     X[l',a,(s,r)]   = sum_l  C[l',l,a] A_i[l,s,r]                   (batched GEMM over l')
+//     M[(l',s'),(r,b)] = sum_{a,s} X[l',a,s,r] W_i[s',a,s,b]          (batched GEMM over l', s')
+//     G = M M^dag ; eigen(G) ; keep k columns U (relative weight tol*zip_tol_factor)
+//     A_i <- U ; C' = U^dag M  (carry [k][r][b] into site i+1)
+//   site 0 starts from the identity carry on (mu, k): the branch index k of the
+//   stacked Kraus MPO multiplies the purification index (matrix addition, Sec. V.A);
+//   right to left, bond i = L-1..1 (compression after the addition, Sec. V.A):
+//     G = M^dag M with M = A_i as [l] x [(s,r)] ; eigen ; keep k rows V^dag (tol, chi_max)
+//     A_i <- V^dag ; A_{i-1} <- A_{i-1} (M V)
+//   purification rank (Sec. IV.A): G = A_0 A_0^dag over mu ; keep the top chi_mu
+//     eigenvectors Y ; A_0 <- Y^dag A_0 / sqrt(kept weight)   (rho / Tr rho, Sec. V.B).
+//
+// Every shape is a DimExpr over the device dims array, so the whole step is a
+// fixed launch sequence (captured once as a CUDA graph) whose kernels read the
+// current bond dimensions from device memory.
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "step.cuh"
+
+namespace qlb {
+
+namespace {
+
+inline unsigned nblk(long n, int t = 256) { return (unsigned)std::max<long>(1, (n + t - 1) / t); }
+
+// z_0 = chi_mu * B, z_L = 1; identity carry C0[(mu*B + k)][mu0][k0] = delta delta;
+// drive coefficient rewrite of the H1 block of core 0; reset per-step stats.
+__global__ void k_step_begin(int* d, int L, int B, zd* C0, long c0_cap, zd* W0, const zd* h1c0, int D1tot,
+                             int drive_off, int drive_D1, const double* f, long long n_f, const long long* step,
+                             double dt, double* stats) {
+  int mu = d[0];
+  int zl = mu * B;
+  long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (tid == 0) {
+    d[L + 1] = zl;
+    d[2 * L + 1] = 1;
+    stats[2] = 0.0;
+  }
+  long n = (long)zl * mu * B;
+  for (long x = tid; x < n && x < c0_cap; x += (long)gridDim.x * blockDim.x) {
+    long lp = x / ((long)mu * B);
+    long rem = x % ((long)mu * B);
+    long mu0 = rem / B, k0 = rem % B;
+    long muv = lp / B, kv = lp % B;
+    C0[x] = mk<double>((muv == mu0 && kv == k0) ? 1.0 : 0.0, 0.0);
+  }
+  if (W0 && h1c0) {
+    long long sidx = *step;
+    double fv = (sidx < n_f) ? f[sidx] : 0.0;
+    zd c = mk<double>(0.0, -dt * fv);  // -i dt f(t_n)
+    // step layout [s'][a][s][b] with a = branch 0; H1 core 0 in builder layout [1][(2s'+s)][j]
+    long ne = 4L * drive_D1;
+    for (long x = tid; x < ne; x += (long)gridDim.x * blockDim.x) {
+      int p = (int)(x / drive_D1), j = (int)(x % drive_D1);
+      int so = p >> 1, si = p & 1;
+      W0[(((long)so * B + 0) * 2 + si) * D1tot + drive_off + j] = cmul(c, h1c0[x]);
+    }
+  }
+}
+
+__global__ void k_step_end(long long* step, int count) {
+  if (count && threadIdx.x == 0 && blockIdx.x == 0) (*step)++;
+}
+
+// z_i = d_i for every bond (truncate-only pass has no zip-up)
+__global__ void k_zip_from_state(int* d, int L) {
+  int i = threadIdx.x;
+  if (i <= L) d[L + 1 + i] = d[i];
+}
+
+// dst[x] = src[x] for x < c * d[a] * d[b]
+__global__ void k_copy(zd* dst, const zd* src, DimExpr cnt, const int* d) {
+  long n = dev_eval(cnt, d);
+  for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < n; x += (long)gridDim.x * blockDim.x) dst[x] = src[x];
+}
+
+__global__ void k_sum_abs2(const zd* p, DimExpr cnt, const int* d, double* out) {
+  __shared__ double sh[32];
+  long n = dev_eval(cnt, d);
+  double acc = 0;
+  for (long x = threadIdx.x; x < n; x += blockDim.x) acc += cabs2(p[x]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) r += sh[w];
+    *out = r;
+  }
+}
+
+// builder layout [a][(2s'+s)][b] -> step layout [s'][a][s][b]
+__global__ void k_to_step_layout(const zd* src, int Da, int Db, zd* dst) {
+  long x = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  long n = (long)Da * 4 * Db;
+  if (x >= n) return;
+  int a = (int)(x / (4L * Db));
+  int rem = (int)(x % (4L * Db));
+  int p = rem / Db, b = rem % Db;
+  int so = p >> 1, si = p & 1;
+  dst[(((long)so * Da + a) * 2 + si) * Db + b] = src[x];
+}
+
+// step layout [s'][a][s][b] -> builder layout [a][(2s'+s)][b], keeping only left index a0 (Da_out = 1)
+__global__ void k_from_step_layout(const zd* src, int Da, int Db, int a0, zd* dst) {
+  long x = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  int Dout = a0 >= 0 ? 1 : Da;
+  long n = (long)Dout * 4 * Db;
+  if (x >= n) return;
+  int a = (int)(x / (4L * Db));
+  int rem = (int)(x % (4L * Db));
+  int p = rem / Db, b = rem % Db;
+  int so = p >> 1, si = p & 1;
+  int as = a0 >= 0 ? a0 : a;
+  dst[x] = src[(((long)so * Da + as) * 2 + si) * Db + b];
+}
+
+// drive coefficient rewrite alone (same formula as in k_step_begin)
+__global__ void k_drive_rewrite(zd* W0, const zd* h1c0, int B, int D1tot, int drive_off, int drive_D1, const double* f,
+                                long long n_f, const long long* step, double dt) {
+  long long sidx = *step;
+  double fv = (sidx < n_f) ? f[sidx] : 0.0;
+  zd c = mk<double>(0.0, -dt * fv);
+  long ne = 4L * drive_D1;
+  for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < ne; x += (long)gridDim.x * blockDim.x) {
+    int p = (int)(x / drive_D1), j = (int)(x % drive_D1);
+    int so = p >> 1, si = p & 1;
+    W0[(((long)so * B + 0) * 2 + si) * D1tot + drive_off + j] = cmul(c, h1c0[x]);
+  }
+}
+
+__global__ void k_identity_core(zd* W) {
+  // step layout [s'][a=1][s][b=1]: delta_{s's}
+  int x = threadIdx.x;
+  if (x < 4) W[x] = mk<double>((x == 0 || x == 3) ? 1.0 : 0.0, 0.0);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launch helpers
+
+static void prof_before(qlb_ctx* ctx, int kclass, cudaEvent_t* a) {
+  *a = nullptr;
+  if (!ctx->prof_on) return;
+  if (ctx->ev_used + 2 > ctx->ev_pool.size()) {
+    for (int i = 0; i < 256; i++) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ctx->ev_pool.push_back(e);
+    }
+  }
+  *a = ctx->ev_pool[ctx->ev_used++];
+  cudaEventRecord(*a, ctx->stream);
+  (void)kclass;
+}
+static void prof_after(qlb_ctx* ctx, int kclass, cudaEvent_t a) {
+  if (!ctx->prof_on || !a) return;
+  cudaEvent_t b = ctx->ev_pool[ctx->ev_used++];
+  cudaEventRecord(b, ctx->stream);
+  ctx->prof_events.push_back({kclass, a, b});
+}
+
+// Opt-in trace for debugging (QLB_DEBUG_DUMP=<file>): after every launch of an
+// uncaptured step, append the dims array and the first entries of the output.
+static FILE* debug_file() {
+  static FILE* f = nullptr;
+  static bool init = false;
+  if (!init) {
+    init = true;
+    const char* p = getenv("QLB_DEBUG_DUMP");
+    if (p && *p) f = fopen(p, "wb");
+  }
+  return f;
+}
+static void debug_dump(qlb_state* st, int tag, const void* out) {
+  FILE* f = debug_file();
+  if (!f) return;
+  cudaStreamCaptureStatus cs;
+  cudaStreamIsCapturing(st->sys->ctx->stream, &cs);
+  if (cs != cudaStreamCaptureStatusNone) return;
+  cudaStreamSynchronize(st->sys->ctx->stream);
+  int n = 2 * st->L + 2;
+  std::vector<int> d(n);
+  cudaMemcpy(d.data(), st->d_dims, sizeof(int) * n, cudaMemcpyDeviceToHost);
+  std::vector<zd> buf(64, mk<double>(0, 0));
+  auto it = g_alloc_sizes().find(const_cast<void*>(out));
+  size_t avail = it == g_alloc_sizes().end() ? 0 : it->second.first / sizeof(zd);
+  cudaMemcpy(buf.data(), out, sizeof(zd) * std::min<size_t>(64, avail), cudaMemcpyDeviceToHost);
+  fwrite(&tag, sizeof(int), 1, f);
+  fwrite(&n, sizeof(int), 1, f);
+  fwrite(d.data(), sizeof(int), n, f);
+  fwrite(buf.data(), sizeof(zd), 64, f);
+  fflush(f);
+}
+
+static qlb_status gemm(qlb_state* st, GemmDesc& g) {
+  qlb_ctx* ctx = st->sys->ctx;
+  cudaEvent_t a;
+  prof_before(ctx, g.kclass, &a);
+  cudaError_t e = launch_gemm<double>(g, st->d_dims, ctx->stream, ctx->prof_on ? ctx->d_prof + g.kclass : nullptr);
+  prof_after(ctx, g.kclass, a);
+  if (e != cudaSuccess) {
+    set_error(std::string("gemm launch: ") + cudaGetErrorString(e));
+    return QLB_EDEVICE;
+  }
+  debug_dump(st, 1, g.C);
+  return QLB_OK;
+}
+
+static qlb_status eig(qlb_state* st, EigDesc& e) {
+  qlb_ctx* ctx = st->sys->ctx;
+  cudaEvent_t a;
+  prof_before(ctx, QLB_K_EIG, &a);
+  cudaError_t r = launch_eig<double>(e, st->d_dims, ctx->stream, st->eigw, ctx->prof_on ? ctx->d_prof + QLB_K_EIG : nullptr);
+  prof_after(ctx, QLB_K_EIG, a);
+  if (r != cudaSuccess) {
+    set_error(std::string("eig launch: ") + cudaGetErrorString(r));
+    return QLB_EDEVICE;
+  }
+  debug_dump(st, 2, e.out);
+  return QLB_OK;
+}
+
+static qlb_status copy(qlb_state* st, zd* dst, const zd* src, DimExpr cnt, long max_n) {
+  qlb_ctx* ctx = st->sys->ctx;
+  cudaEvent_t a;
+  prof_before(ctx, QLB_K_OTHER, &a);
+  k_copy<<<nblk(max_n), 256, 0, ctx->stream>>>(dst, src, cnt, st->d_dims);
+  prof_after(ctx, QLB_K_OTHER, a);
+  QLB_CUDA_TRY(cudaGetLastError());
+  return QLB_OK;
+}
+
+static GemmDesc gdesc() {
+  GemmDesc g{};
+  g.sA1 = g.sB1 = g.sC1 = g.sA2 = g.sB2 = g.sC2 = dconst(0);
+  g.nb1 = g.nb2 = dconst(1);
+  g.nb_max = 1;
+  g.opA = g.opB = OP_N;
+  g.alpha_re = 1.0;
+  g.alpha_im = 0.0;
+  return g;
+}
+
+// ------------------------------------------------------------------ Kraus MPO
+
+Kraus::~Kraus() {
+  for (auto p : W) dev_free(nullptr, p);
+  if (drive_core0) dev_free(nullptr, drive_core0);
+}
+
+static void kraus_clear(qlb_ctx* ctx, Kraus& K) {
+  for (auto p : K.W) dev_free(ctx, p);
+  K.W.clear();
+  if (K.drive_core0) dev_free(ctx, K.drive_core0);
+  K.drive_core0 = nullptr;
+  K.D.clear();
+  K.driven = false;
+  K.dt = -1;
+  K.version = -1;
+}
+
+static qlb_status kraus_from_mpo(qlb_ctx* ctx, const Mpo& S, Kraus& K) {
+  K.L = S.L;
+  K.D = S.D;
+  K.B = S.D[0];
+  K.W.assign(S.L, nullptr);
+  for (int i = 0; i < S.L; i++) {
+    long n = (long)S.D[i] * 4 * S.D[i + 1];
+    qlb_status st = dev_alloc(ctx, (void**)&K.W[i], sizeof(zd) * n);
+    if (st) return st;
+    k_to_step_layout<<<nblk(n), 256, 0, ctx->stream>>>(S.core[i], S.D[i], S.D[i + 1], K.W[i]);
+  }
+  QLB_CUDA_TRY(cudaGetLastError());
+  return QLB_OK;
+}
+
+qlb_status build_identity_kraus(qlb_state* st) {
+  qlb_ctx* ctx = st->sys->ctx;
+  if (st->kraus_id.dt == 0.0 && st->kraus_id.version == -2) return QLB_OK;
+  kraus_clear(ctx, st->kraus_id);
+  Kraus& K = st->kraus_id;
+  K.L = st->L;
+  K.B = 1;
+  K.D.assign(st->L + 1, 1);
+  K.W.assign(st->L, nullptr);
+  for (int i = 0; i < st->L; i++) {
+    qlb_status s = dev_alloc(ctx, (void**)&K.W[i], 4 * sizeof(zd));
+    if (s) return s;
+    k_identity_core<<<1, 32, 0, ctx->stream>>>(K.W[i]);
+  }
+  QLB_CUDA_TRY(cudaGetLastError());
+  K.dt = 0.0;
+  K.version = -2;
+  K.unstable_factor = 0.0;
+  return QLB_OK;
+}
+
+// K_0 = U_1 = 1 - i h H_eff, H_eff = H0 - (i/2) sum_k L_k^dag L_k (Sec. V.B), K_k = sqrt(h) L_k;
+// stacked with branch k on the left boundary and jointly recompressed.  With a
+// drive the H1 block is appended uncompressed on branch 0 and its core 0 is
+// rewritten every step with -i h f(t_n).
+qlb_status build_kraus(qlb_state* st, double dt) {
+  qlb_system* sys = st->sys;
+  qlb_ctx* ctx = sys->ctx;
+  if (st->kraus.dt == dt && st->kraus.version == sys->version) return QLB_OK;
+  if (!sys->H0 && sys->jumps.empty()) {
+    set_error("system has neither a Hamiltonian nor jump operators");
+    return QLB_ESTATE;
+  }
+  kraus_clear(ctx, st->kraus);
+  qlb_status s;
+  // U_1 terms
+  std::vector<DevTerm> terms;
+  std::vector<zd*> tmp;
+  DevTerm id;
+  id.coeff = mk<double>(1.0, 0.0);
+  id.fac.assign(sys->M, nullptr);
+  terms.push_back(id);
+  if (sys->H0)
+    for (auto& t : sys->H0->terms) {
+      DevTerm u = t;
+      u.coeff = cmul(t.coeff, mk<double>(0.0, -dt));
+      terms.push_back(u);
+    }
+  double gamma_bound = 0.0;
+  for (const qlb_op* L : sys->jumps) {
+    gamma_bound += L->inf_norm_bound * L->inf_norm_bound;
+    for (auto& ta : L->terms)
+      for (auto& tb : L->terms) {
+        DevTerm u;
+        // (c_a F_a)^dag (c_b F_b) = conj(c_a) c_b F_a^dag F_b, mode by mode
+        u.coeff = cmul(cconj(ta.coeff), tb.coeff);
+        u.coeff = cscale(u.coeff, -0.5 * dt);  // -i h * (-i/2) = -h/2
+        u.fac.assign(sys->M, nullptr);
+        for (int m = 0; m < sys->M; m++) {
+          int N = 1 << sys->R[m];
+          const zd* A = ta.fac[m];
+          const zd* B = tb.fac[m];
+          if (!A && !B) continue;
+          zd* P = nullptr;
+          if (A && B)
+            s = dense_mul(ctx, A, OP_C, B, N, &P);
+          else if (A) {  // A^dag
+            zd* I = nullptr;
+            qlb_factor f{m, QLB_F_ID, 1, 0.0, nullptr};
+            if ((s = make_factor(ctx, N, f, &I))) return s;
+            s = dense_mul(ctx, A, OP_C, I, N, &P);
+            dev_free(ctx, I);
+          } else {
+            P = nullptr;
+            s = QLB_OK;
+            u.fac[m] = const_cast<zd*>(B);
+            continue;
+          }
+          if (s) return s;
+          tmp.push_back(P);
+          u.fac[m] = P;
+        }
+        terms.push_back(u);
+      }
+  }
+  Mpo U1;
+  s = mpo_from_terms(sys, terms, 1e-30, 0, U1);
+  for (auto p : tmp) dev_free(ctx, p);
+  if (s) return s;
+  // stack U_1 and sqrt(h) L_k
+  std::vector<Mpo> Lk(sys->jumps.size());
+  std::vector<const Mpo*> parts = {&U1};
+  std::vector<int> rows = {0};
+  for (size_t k = 0; k < sys->jumps.size(); k++) {
+    if ((s = mpo_copy(ctx, sys->jumps[k]->mpo, Lk[k]))) return s;
+    if ((s = mpo_scale(ctx, Lk[k], mk<double>(std::sqrt(dt), 0.0)))) return s;
+    parts.push_back(&Lk[k]);
+    rows.push_back((int)k + 1);
+  }
+  int B = 1 + (int)sys->jumps.size();
+  Mpo S;
+  if ((s = mpo_stack(ctx, parts, rows, B, S))) return s;
+  mpo_clear(ctx, U1);
+  for (auto& m : Lk) mpo_clear(ctx, m);
+  if ((s = mpo_compress(ctx, S, 1e-30, 0))) return s;
+  Kraus& K = st->kraus;
+  if (sys->H1) {
+    // append the H1 block on branch 0
+    Mpo H1c;
+    if ((s = mpo_copy(ctx, sys->H1->mpo, H1c))) return s;
+    std::vector<const Mpo*> p2 = {&S, &H1c};
+    Mpo S2;
+    if ((s = mpo_stack(ctx, p2, {0, 0}, B, S2))) return s;
+    K.driven = true;
+    K.drive_off = S.D[1];
+    K.drive_D1 = H1c.D[1];
+    long n0 = 4L * H1c.D[1];
+    if ((s = dev_alloc(ctx, (void**)&K.drive_core0, sizeof(zd) * n0))) return s;
+    QLB_CUDA_TRY(cudaMemcpyAsync(K.drive_core0, H1c.core[0], sizeof(zd) * n0, cudaMemcpyDeviceToDevice, ctx->stream));
+    // H1 core 0 starts at zero in the stacked MPO (rewritten each step)
+    mpo_clear(ctx, H1c);
+    mpo_clear(ctx, S);
+    if ((s = kraus_from_mpo(ctx, S2, K))) return s;
+    mpo_clear(ctx, S2);
+  } else {
+    if ((s = kraus_from_mpo(ctx, S, K))) return s;
+    mpo_clear(ctx, S);
+  }
+  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  K.dt = dt;
+  K.version = sys->version;
+  K.unstable_factor = dt * gamma_bound;
+  return QLB_OK;
+}
+
+// ------------------------------------------------------------------ buffers
+
+static qlb_status realloc_buf(qlb_ctx* ctx, zd** p, size_t* have, size_t need) {
+  if (*p && *have >= need) return QLB_OK;
+  dev_free(ctx, *p);
+  *p = nullptr;
+  *have = 0;
+  qlb_status s = dev_alloc(ctx, (void**)p, sizeof(zd) * std::max<size_t>(need, 1));
+  if (s) return s;
+  *have = need;
+  return QLB_OK;
+}
+
+struct Caps {
+  std::vector<int> dcap, zcap;
+  std::vector<int> hd;  // host mirror of caps in the dims layout
+};
+
+static Caps compute_caps(const qlb_state* st, const std::vector<int>& cur, const Kraus& K) {
+  const int L = st->L;
+  Caps c;
+  c.dcap.assign(L + 1, 1);
+  c.zcap.assign(L + 1, 1);
+  // the purification rank never exceeds the Hilbert-space dimension 2^L
+  c.dcap[0] = std::max(std::min<long>(st->cap_mu, 1L << std::min(L, 30)), (long)cur[0]);
+  for (int i = 1; i < L; i++) {
+    long right = 1L << std::min(L - i, 30);
+    long left = (long)st->cap_mu << std::min(i, 30);
+    long v = std::min<long>({(long)st->cap_chi, right, left});
+    c.dcap[i] = (int)std::max<long>(v, cur[i]);
+  }
+  c.zcap[0] = c.dcap[0] * K.B;
+  // zip-up bond i: rank(M) <= min(2 z_{i-1}, d_i D_i).  It is not bounded by the
+  // right Hilbert dimension 2^(L-i): the right environment of the zip-up holds
+  // the MPO and is no isometry, so M can need more columns than the final Schmidt rank.
+  for (int i = 1; i < L; i++) {
+    long v = std::min<long>({(long)st->cap_chi, 2L * c.zcap[i - 1], (long)c.dcap[i] * K.D[i]});
+    c.zcap[i] = (int)std::max<long>(v, 1);
+    c.zcap[i] = std::max(c.zcap[i], cur[i]);  // truncate-only pass: z_i = d_i
+  }
+  c.hd.assign(2 * L + 2, 1);
+  for (int i = 0; i <= L; i++) {
+    c.hd[SB(i)] = c.dcap[i];
+    c.hd[ZB(st, i)] = c.zcap[i];
+  }
+  return c;
+}
+
+qlb_status plan_buffers(qlb_state* st, const Kraus& K) {
+  qlb_ctx* ctx = st->sys->ctx;
+  const int L = st->L;
+  std::vector<int> cur;
+  qlb_status s;
+  if ((s = read_dims(st, cur))) return s;
+  Caps c = compute_caps(st, cur, K);
+  const std::vector<int>& D = K.D;
+  const int B = K.B;
+  size_t nX = 1, nM = 1, nC = 1, nG = 1, nT = 1;
+  int n_eig = 1;
+  nC = (size_t)c.zcap[0] * c.dcap[0] * B;
+  for (int i = 0; i < L; i++) {
+    nX = std::max(nX, (size_t)c.zcap[i] * D[i] * 2 * c.dcap[i + 1]);
+    nM = std::max(nM, (size_t)2 * c.zcap[i] * c.dcap[i + 1] * D[i + 1]);
+    if (i + 1 <= L) nC = std::max(nC, (size_t)c.zcap[i + 1] * c.dcap[i + 1] * D[i + 1]);
+    if (i < L - 1) {
+      nG = std::max(nG, (size_t)4 * c.zcap[i] * c.zcap[i]);
+      n_eig = std::max(n_eig, 2 * c.zcap[i]);
+    }
+    if (i >= 1) {
+      nG = std::max(nG, (size_t)4 * c.dcap[i + 1] * c.dcap[i + 1]);
+      n_eig = std::max(n_eig, 2 * c.dcap[i + 1]);
+      nT = std::max({nT, (size_t)c.dcap[i] * 2 * c.dcap[i + 1], (size_t)c.zcap[i] * c.dcap[i],
+                     (size_t)2 * c.zcap[i - 1] * c.dcap[i], (size_t)2 * c.zcap[i] * c.dcap[i + 1]});
+    }
+  }
+  nG = std::max(nG, (size_t)c.zcap[0] * c.zcap[0]);
+  n_eig = std::max(n_eig, c.zcap[0]);
+  nT = std::max({nT, (size_t)c.zcap[0] * c.dcap[0], (size_t)c.dcap[0] * 2 * c.dcap[1], (size_t)c.zcap[0] * 2 * c.dcap[1]});
+  if (n_eig > 512) {
+    set_error("a truncation would need an eigen-solve of size " + std::to_string(n_eig) + " (> 512)");
+    return QLB_EINVAL;
+  }
+  if ((s = realloc_buf(ctx, &st->X, &st->nX, nX))) return s;
+  if ((s = realloc_buf(ctx, &st->Mb, &st->nM, nM))) return s;
+  {
+    size_t c1 = st->nC, c2 = st->nC;
+    if ((s = realloc_buf(ctx, &st->Cin, &c1, nC))) return s;
+    if ((s = realloc_buf(ctx, &st->Cout, &c2, nC))) return s;
+    st->nC = std::max(st->nC, nC);
+  }
+  if ((s = realloc_buf(ctx, &st->G, &st->nG, nG))) return s;
+  size_t t1 = st->nT, t2 = st->nT, t3 = st->nT;
+  if ((s = realloc_buf(ctx, &st->T1, &t1, nT))) return s;
+  if ((s = realloc_buf(ctx, &st->T2, &t2, nT))) return s;
+  if ((s = realloc_buf(ctx, &st->T3, &t3, nT))) return s;
+  st->nT = std::max(st->nT, nT);
+  int np = n_eig + (n_eig & 1);
+  size_t new_ew = (eig_smem_bytes<double>(n_eig) > 200 * 1024) ? (size_t)2 * np * np : 1;
+  if ((s = realloc_buf(ctx, &st->eigw, &st->nEw, new_ew))) return s;
+  if (!st->d_lam) {
+    if ((s = dev_alloc(ctx, (void**)&st->d_lam, sizeof(double) * 1024))) return s;
+  }
+  // sites: grow keeping their content
+  for (int i = 0; i < L; i++) {
+    size_t need = (size_t)std::max(c.dcap[i], c.zcap[i]) * 2 * std::max(c.dcap[i + 1], c.zcap[i + 1]);
+    if (need > st->site_cap[i]) {
+      zd* p = nullptr;
+      if ((s = dev_alloc(ctx, (void**)&p, sizeof(zd) * need))) return s;
+      size_t have = (size_t)cur[i] * 2 * cur[i + 1];
+      if (st->site[i] && have)
+        QLB_CUDA_TRY(cudaMemcpyAsync(p, st->site[i], sizeof(zd) * have, cudaMemcpyDeviceToDevice, ctx->stream));
+      dev_free(ctx, st->site[i]);
+      st->site[i] = p;
+      st->site_cap[i] = need;
+    }
+  }
+  // grid bounds only grow, so a graph captured earlier stays valid for smaller plans
+  if (st->cap_state.size() == c.hd.size())
+    for (size_t j = 0; j < c.hd.size(); j++) c.hd[j] = std::max(c.hd[j], st->cap_state[j]);
+  st->cap_state = c.hd;
+  st->plan_key++;
+  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return QLB_OK;
+}
+
+// ------------------------------------------------------------------ the step
+
+static qlb_status enqueue_compress(qlb_state* st, const std::vector<int>& hd) {
+  const int L = st->L;
+  qlb_ctx* ctx = st->sys->ctx;
+  const qlb_options& o = ctx->opt;
+  qlb_status s;
+  auto cap = [&](int idx) { return hd[idx]; };
+  for (int i = L - 1; i >= 1; i--) {
+    // G = M^dag M, M = A_i as [z_i] x [(s, d_{i+1})]
+    GemmDesc g = gdesc();
+    g.kclass = QLB_K_GRAM;
+    g.A = st->site[i];
+    g.B = st->site[i];
+    g.C = st->G;
+    g.m = g.n = dvar(SB(i + 1), 2);
+    g.k = dvar(ZB(st, i));
+    g.opA = OP_C;
+    g.lda = dvar(SB(i + 1), 2);
+    g.ldb = dvar(SB(i + 1), 2);
+    g.ldc = dvar(SB(i + 1), 2);
+    g.m_max = g.n_max = 2 * cap(SB(i + 1));
+    if ((s = gemm(st, g))) return s;
+    EigDesc e{};
+    e.G = st->G;
+    e.lam = nullptr;
+    e.n = dvar(SB(i + 1), 2);
+    e.n_max = 2 * cap(SB(i + 1));
+    e.out = st->T1;
+    e.out_mode = 1;
+    e.dim_out = SB(i);
+    e.tol = st->tol;
+    e.cap = dconst(std::min(st->chi_max, cap(SB(i))));
+    e.gap = o.degeneracy_gap;
+    e.max_sweeps = o.max_sweeps;
+    e.disc_stat = st->d_stats + 2;
+    e.err = st->d_err;
+    if ((s = eig(st, e))) return s;
+    // US = M V_k  (V_k = T1^dag)
+    g = gdesc();
+    g.kclass = QLB_K_APPLY;
+    g.A = st->site[i];
+    g.B = st->T1;
+    g.C = st->T2;
+    g.m = dvar(ZB(st, i));
+    g.n = dvar(SB(i));
+    g.k = dvar(SB(i + 1), 2);
+    g.opB = OP_C;
+    g.lda = dvar(SB(i + 1), 2);
+    g.ldb = dvar(SB(i + 1), 2);
+    g.ldc = dvar(SB(i));
+    g.m_max = cap(ZB(st, i));
+    g.n_max = cap(SB(i));
+    if ((s = gemm(st, g))) return s;
+    if ((s = copy(st, st->site[i], st->T1, dvar2(SB(i), SB(i + 1), 2), (long)cap(SB(i)) * 2 * cap(SB(i + 1)))))
+      return s;
+    // A_{i-1} <- A_{i-1} US
+    g = gdesc();
+    g.kclass = QLB_K_APPLY;
+    g.A = st->site[i - 1];
+    g.B = st->T2;
+    g.C = st->T3;
+    g.m = dvar(ZB(st, i - 1), 2);
+    g.n = dvar(SB(i));
+    g.k = dvar(ZB(st, i));
+    g.lda = dvar(ZB(st, i));
+    g.ldb = dvar(SB(i));
+    g.ldc = dvar(SB(i));
+    g.m_max = 2 * cap(ZB(st, i - 1));
+    g.n_max = cap(SB(i));
+    if ((s = gemm(st, g))) return s;
+    if ((s = copy(st, st->site[i - 1], st->T3, dvar2(ZB(st, i - 1), SB(i), 2),
+                  (long)2 * cap(ZB(st, i - 1)) * cap(SB(i)))))
+      return s;
+  }
+  // purification rank: G = A_0 A_0^dag over mu' = z_0
+  {
+    GemmDesc g = gdesc();
+    g.kclass = QLB_K_GRAM;
+    g.A = st->site[0];
+    g.B = st->site[0];
+    g.C = st->G;
+    g.m = g.n = dvar(ZB(st, 0));
+    g.k = dvar(SB(1), 2);
+    g.opB = OP_C;
+    g.lda = g.ldb = dvar(SB(1), 2);
+    g.ldc = dvar(ZB(st, 0));
+    g.m_max = g.n_max = cap(ZB(st, 0));
+    if ((s = gemm(st, g))) return s;
+    EigDesc e{};
+    e.G = st->G;
+    e.lam = st->d_lam;
+    e.n = dvar(ZB(st, 0));
+    e.n_max = cap(ZB(st, 0));
+    e.out = st->T1;
+    e.out_mode = 0;
+    e.dim_out = SB(0);
+    e.tol = st->tol;
+    e.cap = dconst(std::min(st->chi_mu_max, cap(SB(0))));
+    e.gap = o.degeneracy_gap;
+    e.max_sweeps = o.max_sweeps;
+    e.kept_weight = st->d_stats + 0;
+    e.total_weight = st->d_stats + 1;
+    e.err = st->d_err;
+    if ((s = eig(st, e))) return s;
+    g = gdesc();
+    g.kclass = QLB_K_APPLY;
+    g.A = st->T1;
+    g.B = st->site[0];
+    g.C = st->T2;
+    g.m = dvar(SB(0));
+    g.n = dvar(SB(1), 2);
+    g.k = dvar(ZB(st, 0));
+    g.opA = OP_C;
+    g.lda = dvar(SB(0));
+    g.ldb = dvar(SB(1), 2);
+    g.ldc = dvar(SB(1), 2);
+    g.alpha_scale = st->d_stats + 0;
+    g.alpha_scale_rsqrt = 1;
+    g.m_max = cap(SB(0));
+    g.n_max = 2 * cap(SB(1));
+    if ((s = gemm(st, g))) return s;
+    if ((s = copy(st, st->site[0], st->T2, dvar2(SB(0), SB(1), 2), (long)cap(SB(0)) * 2 * cap(SB(1))))) return s;
+  }
+  return QLB_OK;
+}
+
+qlb_status enqueue_step(qlb_state* st, const Kraus& K, bool count_step) {
+  const int L = st->L;
+  qlb_ctx* ctx = st->sys->ctx;
+  const qlb_options& o = ctx->opt;
+  const std::vector<int>& hd = st->cap_state;
+  auto cap = [&](int idx) { return hd[idx]; };
+  qlb_status s;
+  {
+    cudaEvent_t a;
+    prof_before(ctx, QLB_K_OTHER, &a);
+    long n0 = (long)cap(ZB(st, 0)) * cap(SB(0)) * K.B;
+    k_step_begin<<<nblk(n0), 256, 0, ctx->stream>>>(
+        st->d_dims, L, K.B, st->Cin, (long)st->nC, K.driven ? K.W[0] : nullptr, K.driven ? K.drive_core0 : nullptr,
+        K.D[1], K.drive_off, K.drive_D1, st->sys->d_f, st->sys->n_f, st->d_step, K.dt, st->d_stats);
+    prof_after(ctx, QLB_K_OTHER, a);
+    QLB_CUDA_TRY(cudaGetLastError());
+  }
+  zd* Cin = st->Cin;
+  zd* Cout = st->Cout;
+  for (int i = 0; i < L; i++) {
+    const int Dl = K.D[i], Dr = K.D[i + 1];
+    // stage 1: X_l'[a][(s,r)] = sum_l C_l'[l][a] A[l][(s,r)]
+    GemmDesc g = gdesc();
+    g.kclass = QLB_K_CONTRACT;
+    g.A = Cin;
+    g.B = st->site[i];
+    g.C = st->X;
+    g.m = dconst(Dl);
+    g.n = dvar(SB(i + 1), 2);
+    g.k = dvar(SB(i));
+    g.opA = OP_T;
+    g.lda = dconst(Dl);
+    g.ldb = dvar(SB(i + 1), 2);
+    g.ldc = dvar(SB(i + 1), 2);
+    g.sA1 = dvar(SB(i), Dl);
+    g.sC1 = dvar(SB(i + 1), 2 * Dl);
+    g.nb1 = dvar(ZB(st, i));
+    g.m_max = Dl;
+    g.n_max = 2 * cap(SB(i + 1));
+    g.nb_max = cap(ZB(st, i));
+    if ((s = gemm(st, g))) return s;
+    // stage 2: M[(l',s')][(r,b)] = sum_{a,s} X_l'[(a,s)][r] W_s'[(a,s)][b]
+    zd* Mdst = (i == L - 1) ? st->site[L - 1] : st->Mb;
+    g = gdesc();
+    g.kclass = QLB_K_CONTRACT;
+    g.A = st->X;
+    g.B = K.W[i];
+    g.C = Mdst;
+    g.m = dvar(SB(i + 1));
+    g.n = dconst(Dr);
+    g.k = dconst(2 * Dl);
+    g.opA = OP_T;
+    g.lda = dvar(SB(i + 1));
+    g.ldb = dconst(Dr);
+    g.ldc = dconst(Dr);
+    g.sA1 = dvar(SB(i + 1), 2 * Dl);
+    g.sB2 = dconst(Dl * 2 * Dr);
+    g.sC1 = dvar(SB(i + 1), 2 * Dr);
+    g.sC2 = dvar(SB(i + 1), Dr);
+    g.nb1 = dvar(ZB(st, i));
+    g.nb2 = dconst(2);
+    g.m_max = cap(SB(i + 1));
+    g.n_max = Dr;
+    g.nb_max = 2 * cap(ZB(st, i));
+    if ((s = gemm(st, g))) return s;
+    if (i == L - 1) break;
+    // Gram G = M M^dag  ((2 z_i) x (2 z_i), K = d_{i+1} Dr)
+    g = gdesc();
+    g.kclass = QLB_K_GRAM;
+    g.A = st->Mb;
+    g.B = st->Mb;
+    g.C = st->G;
+    g.m = g.n = dvar(ZB(st, i), 2);
+    g.k = dvar(SB(i + 1), Dr);
+    g.opB = OP_C;
+    g.lda = g.ldb = dvar(SB(i + 1), Dr);
+    g.ldc = dvar(ZB(st, i), 2);
+    g.m_max = g.n_max = 2 * cap(ZB(st, i));
+    if ((s = gemm(st, g))) return s;
+    EigDesc e{};
+    e.G = st->G;
+    e.n = dvar(ZB(st, i), 2);
+    e.n_max = 2 * cap(ZB(st, i));
+    e.out = st->site[i];
+    e.out_mode = 0;
+    e.dim_out = ZB(st, i + 1);
+    e.tol = st->tol * o.zip_tol_factor;
+    e.cap = dconst(std::min(st->chi_max, cap(ZB(st, i + 1))));
+    e.gap = o.degeneracy_gap;
+    e.max_sweeps = o.max_sweeps;
+    e.err = st->d_err;
+    if ((s = eig(st, e))) return s;
+    // carry C' = U^dag M  -> [k][(r, b)]
+    g = gdesc();
+    g.kclass = QLB_K_APPLY;
+    g.A = st->site[i];
+    g.B = st->Mb;
+    g.C = Cout;
+    g.m = dvar(ZB(st, i + 1));
+    g.n = dvar(SB(i + 1), Dr);
+    g.k = dvar(ZB(st, i), 2);
+    g.opA = OP_C;
+    g.lda = dvar(ZB(st, i + 1));
+    g.ldb = dvar(SB(i + 1), Dr);
+    g.ldc = dvar(SB(i + 1), Dr);
+    g.m_max = cap(ZB(st, i + 1));
+    g.n_max = cap(SB(i + 1)) * Dr;
+    if ((s = gemm(st, g))) return s;
+    std::swap(Cin, Cout);
+  }
+  if ((s = enqueue_compress(st, hd))) return s;
+  {
+    cudaEvent_t a;
+    prof_before(ctx, QLB_K_OTHER, &a);
+    k_step_end<<<1, 32, 0, ctx->stream>>>(st->d_step, count_step ? 1 : 0);
+    prof_after(ctx, QLB_K_OTHER, a);
+    QLB_CUDA_TRY(cudaGetLastError());
+  }
+  return QLB_OK;
+}
+
+qlb_status read_dims(qlb_state* st, std::vector<int>& d) {
+  qlb_ctx* ctx = st->sys->ctx;
+  d.assign(2 * st->L + 2, 0);
+  QLB_CUDA_TRY(cudaMemcpyAsync(d.data(), st->d_dims, sizeof(int) * d.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return QLB_OK;
+}
+
+qlb_status run_steps(qlb_state* st, int64_t n, bool sync) {
+  qlb_ctx* ctx = st->sys->ctx;
+  qlb_status s;
+  if (n <= 0) return QLB_OK;
+  if (ctx->prof_on || debug_file()) {
+    for (int64_t k = 0; k < n; k++)
+      if ((s = enqueue_step(st, st->kraus, true))) return s;
+  } else {
+    if (!st->graph || st->graph_key != st->plan_key) {
+      if (st->graph) cudaGraphExecDestroy(st->graph);
+      st->graph = nullptr;
+      cudaGraph_t gr;
+      QLB_CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      s = enqueue_step(st, st->kraus, true);
+      cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+      if (s) {
+        if (e == cudaSuccess) cudaGraphDestroy(gr);
+        return s;
+      }
+      QLB_CUDA_TRY(e);
+      e = cudaGraphInstantiate(&st->graph, gr, 0);
+      cudaGraphDestroy(gr);
+      QLB_CUDA_TRY(e);
+      st->graph_key = st->plan_key;
+    }
+    for (int64_t k = 0; k < n; k++) QLB_CUDA_TRY(cudaGraphLaunch(st->graph, ctx->stream));
+  }
+  st->host_steps += n;
+  if (!sync) return QLB_OK;
+  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  int err = 0;
+  QLB_CUDA_TRY(cudaMemcpy(&err, st->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    QLB_CUDA_TRY(cudaMemset(st->d_err, 0, sizeof(int)));
+    if (err & 2) {
+      set_error("non-finite values met in a truncation");
+      return QLB_ENONFINITE;
+    }
+    set_error("a Jacobi eigen-solve hit its sweep limit");
+    return QLB_ENOTCONV;
+  }
+  double stats[2];
+  QLB_CUDA_TRY(cudaMemcpy(stats, st->d_stats, sizeof(stats), cudaMemcpyDeviceToHost));
+  if (!std::isfinite(stats[1])) {
+    set_error("non-finite trace");
+    return QLB_ENONFINITE;
+  }
+  return QLB_OK;
+}
+
+// Truncate-only pass: one sweep with the identity Kraus MPO, then the checks.
+qlb_status truncate_pass(qlb_state* st) {
+  qlb_status s;
+  if ((s = build_identity_kraus(st))) return s;
+  if ((s = plan_buffers(st, st->kraus_id))) return s;
+  if ((s = enqueue_step(st, st->kraus_id, false))) return s;
+  qlb_ctx* ctx = st->sys->ctx;
+  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  int err = 0;
+  QLB_CUDA_TRY(cudaMemcpy(&err, st->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    QLB_CUDA_TRY(cudaMemset(st->d_err, 0, sizeof(int)));
+    set_error(err & 2 ? "non-finite values met in a truncation" : "a Jacobi eigen-solve hit its sweep limit");
+    return err & 2 ? QLB_ENONFINITE : QLB_ENOTCONV;
+  }
+  return QLB_OK;
+}
+
+// ------------------------------------------------------------------ observables
+
+// Tr(O rho) by the transfer E[l'][l][a] (bra, ket, MPO bond):
+//   Y_l'[a][(s,r)] = sum_l E_l'[l][a] A[l][(s,r)]
+//   Z[(l',s')][(r,b)] = sum_{a,s} Y_l'[(a,s)][r] W_s'[(a,s)][b]
+//   E'[r'][(r,b)] = sum_{(l',s')} conj(A[(l',s')][r']) Z[(l',s')][(r,b)]
+// starting from E[mu'][mu][0] = delta (trace over the purification index).
+qlb_status expectation_mpo(qlb_state* st, const Mpo& Wb, double* out) {
+  qlb_ctx* ctx = st->sys->ctx;
+  const int L = st->L;
+  std::vector<int> d;
+  qlb_status s;
+  if ((s = read_dims(st, d))) return s;
+  // op in step layout
+  std::vector<zd*> W(L, nullptr);
+  std::vector<zd*> bufs;
+  auto cleanup = [&]() {
+    for (auto p : W) dev_free(ctx, p);
+    for (auto p : bufs) dev_free(ctx, p);
+  };
+  for (int i = 0; i < L; i++) {
+    long n = (long)Wb.D[i] * 4 * Wb.D[i + 1];
+    if ((s = dev_alloc(ctx, (void**)&W[i], sizeof(zd) * n))) {
+      cleanup();
+      return s;
+    }
+    k_to_step_layout<<<nblk(n), 256, 0, ctx->stream>>>(Wb.core[i], Wb.D[i], Wb.D[i + 1], W[i]);
+  }
+  size_t nE = 1, nY = 1, nZ = 1;
+  for (int i = 0; i < L; i++) {
+    nE = std::max(nE, (size_t)d[i] * d[i] * Wb.D[i]);
+    nE = std::max(nE, (size_t)d[i + 1] * d[i + 1] * Wb.D[i + 1]);
+    nY = std::max(nY, (size_t)d[i] * Wb.D[i] * 2 * d[i + 1]);
+    nZ = std::max(nZ, (size_t)d[i] * 2 * d[i + 1] * Wb.D[i + 1]);
+  }
+  zd *E0, *E1, *Y, *Z;
+  if ((s = dev_alloc(ctx, (void**)&E0, sizeof(zd) * nE)) || (bufs.push_back(E0), 0) ||
+      (s = dev_alloc(ctx, (void**)&E1, sizeof(zd) * nE)) || (bufs.push_back(E1), 0) ||
+      (s = dev_alloc(ctx, (void**)&Y, sizeof(zd) * nY)) || (bufs.push_back(Y), 0) ||
+      (s = dev_alloc(ctx, (void**)&Z, sizeof(zd) * nZ)) || (bufs.push_back(Z), 0)) {
+    cleanup();
+    return s;
+  }
+  {
+    std::vector<zd> h((size_t)d[0] * d[0], mk<double>(0, 0));
+    for (int m = 0; m < d[0]; m++) h[(size_t)m * d[0] + m] = mk<double>(1, 0);
+    QLB_CUDA_TRY(cudaMemcpyAsync(E0, h.data(), sizeof(zd) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  }
+  for (int i = 0; i < L; i++) {
+    int l = d[i], r = d[i + 1], Dl = Wb.D[i], Dr = Wb.D[i + 1];
+    GemmDesc g = gdesc();
+    g.A = E0;
+    g.B = st->site[i];
+    g.C = Y;
+    g.m = dconst(Dl);
+    g.n = dconst(2 * r);
+    g.k = dconst(l);
+    g.opA = OP_T;
+    g.lda = dconst(Dl);
+    g.ldb = dconst(2 * r);
+    g.ldc = dconst(2 * r);
+    g.sA1 = dconst(l * Dl);
+    g.sC1 = dconst(Dl * 2 * r);
+    g.nb1 = dconst(l);
+    g.m_max = Dl;
+    g.n_max = 2 * r;
+    g.nb_max = l;
+    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, ctx->stream, nullptr));
+    g = gdesc();
+    g.A = Y;
+    g.B = W[i];
+    g.C = Z;
+    g.m = dconst(r);
+    g.n = dconst(Dr);
+    g.k = dconst(2 * Dl);
+    g.opA = OP_T;
+    g.lda = dconst(r);
+    g.ldb = dconst(Dr);
+    g.ldc = dconst(Dr);
+    g.sA1 = dconst(2 * Dl * r);
+    g.sB2 = dconst(Dl * 2 * Dr);
+    g.sC1 = dconst(2 * r * Dr);
+    g.sC2 = dconst(r * Dr);
+    g.nb1 = dconst(l);
+    g.nb2 = dconst(2);
+    g.m_max = r;
+    g.n_max = Dr;
+    g.nb_max = 2 * l;
+    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, ctx->stream, nullptr));
+    g = gdesc();
+    g.A = st->site[i];
+    g.B = Z;
+    g.C = E1;
+    g.m = dconst(r);
+    g.n = dconst(r * Dr);
+    g.k = dconst(2 * l);
+    g.opA = OP_C;
+    g.lda = dconst(r);
+    g.ldb = dconst(r * Dr);
+    g.ldc = dconst(r * Dr);
+    g.m_max = r;
+    g.n_max = r * Dr;
+    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, ctx->stream, nullptr));
+    std::swap(E0, E1);
+  }
+  zd res;
+  QLB_CUDA_TRY(cudaMemcpyAsync(&res, E0, sizeof(zd), cudaMemcpyDeviceToHost, ctx->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  cleanup();
+  out[0] = res.re;
+  out[1] = res.im;
+  return QLB_OK;
+}
+
+// Branch k of the stacked Kraus MPO (with the drive coefficient of the state's
+// current step written in) as a builder-layout MPO with left boundary 1.
+qlb_status kraus_branch(qlb_state* st, int k, Mpo& out) {
+  qlb_ctx* ctx = st->sys->ctx;
+  const Kraus& K = st->kraus;
+  if (k < 0 || k >= K.B) {
+    set_error("branch index out of range");
+    return QLB_EINVAL;
+  }
+  if (K.driven)
+    k_drive_rewrite<<<1, 256, 0, ctx->stream>>>(K.W[0], K.drive_core0, K.B, K.D[1], K.drive_off, K.drive_D1,
+                                                st->sys->d_f, st->sys->n_f, st->d_step, K.dt);
+  mpo_clear(ctx, out);
+  out.L = K.L;
+  out.D = K.D;
+  out.D[0] = 1;
+  out.core.assign(K.L, nullptr);
+  for (int i = 0; i < K.L; i++) {
+    long n = (long)out.D[i] * 4 * out.D[i + 1];
+    qlb_status s = dev_alloc(ctx, (void**)&out.core[i], sizeof(zd) * n);
+    if (s) return s;
+    k_from_step_layout<<<nblk(n), 256, 0, ctx->stream>>>(K.W[i], K.D[i], K.D[i + 1], i == 0 ? k : -1, out.core[i]);
+  }
+  QLB_CUDA_TRY(cudaGetLastError());
+  return QLB_OK;
+}
+
+qlb_status state_sum_abs2_site0(qlb_state* st, double* out) {
+  qlb_ctx* ctx = st->sys->ctx;
+  double* d = st->d_stats + 3;
+  k_sum_abs2<<<1, 256, 0, ctx->stream>>>(st->site[0], dvar2(SB(0), SB(1), 2), st->d_dims, d);
+  QLB_CUDA_TRY(cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return QLB_OK;
+}
+
+}  // namespace qlb

@@ -1,0 +1,32 @@
+// Step planning and enqueueing (internal).
+#pragma once
+
+#include "builder.cuh"
+
+namespace qlb {
+
+inline int SB(int i) { return i; }                 // state bond i (0..L)
+inline int ZB(const qlb_state* st, int i) { return st->L + 1 + i; }  // zip-up bond i (0..L)
+
+// Builds (or reuses) the stacked Kraus MPO of the system for time step dt.
+qlb_status build_kraus(qlb_state* st, double dt);
+// The identity "Kraus" MPO (one branch, bond 1) used by truncate-only passes.
+qlb_status build_identity_kraus(qlb_state* st);
+// Sizes every buffer of the state for its current Kraus MPO and caps.
+qlb_status plan_buffers(qlb_state* st, const Kraus& K);
+// Enqueues one full step (apply + stack + recompress + purify + renormalise).
+qlb_status enqueue_step(qlb_state* st, const Kraus& K, bool count_step);
+// One recompression pass with the identity Kraus MPO (truncate / init).
+qlb_status truncate_pass(qlb_state* st);
+// Sum |A_0|^2 (= Tr rho for a right-canonical state).
+qlb_status state_sum_abs2_site0(qlb_state* st, double* out);
+// Runs n steps (CUDA graph unless profiling) and checks the device error flags.
+qlb_status run_steps(qlb_state* st, int64_t n, bool sync);
+// Host copy of the state bonds.
+qlb_status read_dims(qlb_state* st, std::vector<int>& d);
+// Branch k of the current Kraus MPO as a builder-layout MPO (left boundary 1).
+qlb_status kraus_branch(qlb_state* st, int k, Mpo& out);
+// Tr(O rho) with an MPO in builder layout (left boundary 1).
+qlb_status expectation_mpo(qlb_state* st, const Mpo& W, double* out);
+
+}  // namespace qlb

@@ -102,3 +102,15 @@ def random_vector(n: int, seed: int) -> np.ndarray:
     """Seeded complex Gaussian vector (not normalised)."""
     rng = np.random.default_rng(seed)
     return rng.normal(size=n) + 1j * rng.normal(size=n)
+
+
+def transmon_ground_charge(Nt: int, offset: int, ec: float, ej: float, ng: float = 0.0) -> np.ndarray:
+    """Initial transmon vector of the transmon system: the lowest eigenvector of
+    4 Ec (n - ng)^2 - Ej cos(phi) on the charge states n = j - offset (Sec. VII,
+    Eq. transmon), cut open at both ends."""
+    n = np.arange(Nt) - offset
+    H = np.diag(4 * ec * (n - ng) ** 2).astype(np.complex128)
+    for j in range(Nt - 1):
+        H[j, j + 1] = H[j + 1, j] = -ej / 2
+    w, v = np.linalg.eigh(H)
+    return v[:, 0]

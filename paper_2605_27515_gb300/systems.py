@@ -1,0 +1,116 @@
+"""The paper's model systems as C-ABI term lists (argument marshalling only).
+
+Each builder turns a parameter set from ``inputs`` into qlb operators made of the
+library's built-in factors (a, a^dag, n, parity, charge, cos phi) and registers
+the Hamiltonian and jump operators on a ``qlb.System``.  The dense matrices are
+generated on the device by the library.
+
+  cat        H = eps_z (a + a^dag);  L1 = sqrt(k2) (a^2 - alpha^2);  L2 = sqrt(k1) a
+             (cat qubit with two-photon dissipation, Sec. VI, Eq. Hz)
+  transmon   H0 = 4 Ec n_t^2 - Ej cos(phi_t) + w_r a^dag a + g n_t (a + a^dag),
+             H1 = (a + a^dag) with f(t) = eps(t) cos(w_r t);  L = sqrt(kappa) a
+             (Sec. VII, Eq. transmon_cavity with the coupling written as n_t (a + a^dag))
+  cat_pair   modes [b1, a1, a2, b2]: H = sum_i g2 (a_i^2 b_i^dag + a_i^dag^2 b_i)
+             + eps_b (b_i + b_i^dag) + J (a1^dag a2 + a2^dag a1);
+             L = sqrt(kb) b_i, sqrt(k1) a_i  (Sec. VI, Eq. cb, two cats coupled)
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import inputs
+from . import qlb as Q
+
+
+def vacuum(N):
+    v = np.zeros(N, dtype=np.complex128)
+    v[0] = 1.0
+    return v
+
+
+class Built:
+    def __init__(self, sys, ops, init, observables, cfg, f_table=None):
+        self.sys = sys
+        self.ops = ops  # name -> Op (keeps them alive)
+        self.init = init  # list of mode vectors
+        self.observables = observables  # name -> Op
+        self.cfg = cfg
+        self.f_table = f_table
+
+
+def build_cat(ctx, cfg):
+    R = cfg["R"][0]
+    s = Q.System(ctx, [R])
+    a2, k2, k1, ez = cfg["alpha2"], cfg["k2"], cfg["k1"], cfg.get("eps_z", 0.0)
+    ops = {}
+    if ez:
+        ops["H"] = s.op([(ez, [(0, Q.F_A)]), (ez, [(0, Q.F_ADAG)])])
+        s.set_hamiltonian(ops["H"])
+    ops["L1"] = s.op([(np.sqrt(k2), [(0, Q.F_A, 2)]), (-np.sqrt(k2) * a2, [])])
+    s.add_jump(ops["L1"])
+    if k1:
+        ops["L2"] = s.op([(np.sqrt(k1), [(0, Q.F_A)])])
+        s.add_jump(ops["L2"])
+    obs = {"n": s.op([(1.0, [(0, Q.F_NUM)])]), "parity": s.op([(1.0, [(0, Q.F_PARITY)])])}
+    return Built(s, ops, [vacuum(2 ** R)], obs, cfg)
+
+
+def build_transmon(ctx, cfg, nsteps=None):
+    Rt, Rr = cfg["R"]
+    Nt = 2 ** Rt
+    off = Nt // 2
+    s = Q.System(ctx, [Rt, Rr])
+    ec = cfg["ec"]
+    ej = cfg["ej_over_ec"] * ec
+    g = cfg["g_over_ec"] * ec
+    ops = {}
+    ops["H0"] = s.op([
+        (4 * ec, [(0, Q.F_CHARGE, 2, float(off) + cfg.get("ng", 0.0))]),
+        (-ej, [(0, Q.F_COSPHI)]),
+        (cfg["wr"], [(1, Q.F_NUM)]),
+        (g, [(0, Q.F_CHARGE, 1, float(off)), (1, Q.F_A)]),
+        (g, [(0, Q.F_CHARGE, 1, float(off)), (1, Q.F_ADAG)]),
+    ])
+    ops["H1"] = s.op([(1.0, [(1, Q.F_A)]), (1.0, [(1, Q.F_ADAG)])])
+    n = nsteps if nsteps is not None else cfg["steps"]
+    f = inputs.transmon_drive_table(cfg, n)
+    s.set_hamiltonian(ops["H0"], ops["H1"], f)
+    ops["L"] = s.op([(np.sqrt(cfg["kappa"]), [(1, Q.F_A)])])
+    s.add_jump(ops["L"])
+    obs = {"n_c": s.op([(1.0, [(1, Q.F_NUM)])]), "n_t2": s.op([(1.0, [(0, Q.F_CHARGE, 2, float(off))])])}
+    init = [inputs.transmon_ground_charge(Nt, off, ec, ej, cfg.get("ng", 0.0)), vacuum(2 ** Rr)]
+    return Built(s, ops, init, obs, cfg, f)
+
+
+def build_cat_pair(ctx, cfg, J=None):
+    Rb1, Ra1, Ra2, Rb2 = cfg["R"][1], cfg["R"][0], cfg["R"][2], cfg["R"][3]
+    s = Q.System(ctx, [Rb1, Ra1, Ra2, Rb2])
+    b1, a1, a2, b2 = 0, 1, 2, 3
+    g2, kb, k1 = cfg["g2"], cfg["kb"], cfg["k1"]
+    eb = -g2 * cfg["alpha2"]
+    J = cfg["J"] if J is None else J
+    terms = []
+    for a, b in ((a1, b1), (a2, b2)):
+        terms += [(g2, [(a, Q.F_A, 2), (b, Q.F_ADAG)]), (g2, [(a, Q.F_ADAG, 2), (b, Q.F_A)]),
+                  (eb, [(b, Q.F_A)]), (eb, [(b, Q.F_ADAG)])]
+    terms += [(J, [(a1, Q.F_ADAG), (a2, Q.F_A)]), (J, [(a2, Q.F_ADAG), (a1, Q.F_A)])]
+    ops = {"H": s.op(terms)}
+    s.set_hamiltonian(ops["H"])
+    for name, m, k in (("Lb1", b1, kb), ("Lb2", b2, kb), ("La1", a1, k1), ("La2", a2, k1)):
+        ops[name] = s.op([(np.sqrt(k), [(m, Q.F_A)])])
+        s.add_jump(ops[name])
+    obs = {"n_a1": s.op([(1.0, [(a1, Q.F_NUM)])]), "n_a2": s.op([(1.0, [(a2, Q.F_NUM)])]),
+           "parity_a1": s.op([(1.0, [(a1, Q.F_PARITY)])])}
+    init = [vacuum(2 ** r) for r in s.R]
+    return Built(s, ops, init, obs, cfg)
+
+
+def build(ctx, cfg, **kw):
+    kind = cfg["kind"]
+    if kind == "cat":
+        return build_cat(ctx, cfg)
+    if kind == "transmon":
+        return build_transmon(ctx, cfg, **kw)
+    if kind == "cat_pair":
+        return build_cat_pair(ctx, cfg, **kw)
+    raise ValueError(kind)
