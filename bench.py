@@ -174,6 +174,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")
         with torch.cuda.stream(stream):
             for k in range(args.steps):
                 flush.fill_(float(k))
@@ -181,6 +182,7 @@ def run_gpu(args):
                 status = max(status, st.step(dt, 1))
                 evs[k][1].record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     ms = [a.elapsed_time(bb) for a, bb in evs]
     total_ms = float(sum(ms))
     if world > 1:

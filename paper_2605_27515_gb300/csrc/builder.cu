@@ -149,6 +149,78 @@ __global__ void __launch_bounds__(B_THREADS) k_osj_round(zd* X, int m, int n, zd
   }
 }
 
+// All sweeps of the row-wise one-sided Jacobi in one CTA (for moderate sizes):
+// warp w rotates the pairs w, w + 32, ... of each round; rounds are separated by
+// __syncthreads().  Stops after a sweep without rotation or after max_sweeps;
+// writes the number of sweeps run, or -1 when it stopped at the limit.
+constexpr int OSJ1_THREADS = 1024;
+__global__ void __launch_bounds__(OSJ1_THREADS) k_osj_all(zd* X, int m, int n, zd* T, const double* abs_thr_p,
+                                                        int max_sweeps, int* sweeps_out) {
+  __shared__ int s_rot;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = OSJ1_THREADS >> 5;
+  const int np = m + (m & 1);
+  const double abs_thr = *abs_thr_p;
+  const double rel = 2.220446049250313e-16 * fmax(8.0, 4.0 * sqrt((double)n));
+  int sw = 0;
+  for (; sw < max_sweeps; sw++) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < np - 1; round++) {
+      for (int t = warp; t < np / 2; t += nwarps) {
+        int p = rr_player_b(t, round, np), q = rr_player_b(np - 1 - t, round, np);
+        if (p > q) {
+          int x = p;
+          p = q;
+          q = x;
+        }
+        if (q >= m) continue;
+        zd* xp = X + (long)p * n;
+        zd* xq = X + (long)q * n;
+        double a = 0, b = 0, gr = 0, gi = 0;
+        for (int j = lane; j < n; j += 32) {
+          zd u = xp[j], v = xq[j];
+          a += u.re * u.re + u.im * u.im;
+          b += v.re * v.re + v.im * v.im;
+          gr += u.re * v.re + u.im * v.im;
+          gi += u.im * v.re - u.re * v.im;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          gr += __shfl_xor_sync(0xffffffffu, gr, o);
+          gi += __shfl_xor_sync(0xffffffffu, gi, o);
+        }
+        double x = sqrt(gr * gr + gi * gi);
+        if (!(x > 0.0 && x > rel * sqrt(a * b) && x > abs_thr)) continue;
+        double tau = (b - a) / (2 * x);
+        double tt = fabs(tau) > 1e100 ? 0.5 / tau : (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double c = 1.0 / sqrt(1.0 + tt * tt);
+        double s = tt * c;
+        zd sp = mk<double>(s * gr / x, s * gi / x);
+        for (int j = lane; j < n; j += 32) {
+          zd u = xp[j], v = xq[j];
+          xp[j] = csub(cscale(u, c), cmul(sp, v));
+          xq[j] = cadd(cmul(cconj(sp), u), cscale(v, c));
+        }
+        zd* tp = T + (long)p * m;
+        zd* tq = T + (long)q * m;
+        for (int j = lane; j < m; j += 32) {
+          zd u = tp[j], v = tq[j];
+          tp[j] = csub(cscale(u, c), cmul(sp, v));
+          tq[j] = cadd(cmul(cconj(sp), u), cscale(v, c));
+        }
+        if (lane == 0) atomicAdd(&s_rot, 1);
+      }
+      __syncthreads();
+    }
+    int nr = s_rot;
+    __syncthreads();
+    if (nr == 0) break;
+  }
+  if (threadIdx.x == 0) *sweeps_out = (sw < max_sweeps) ? sw + 1 : -1;
+}
+
 __global__ void k_abs_thr(const zd* X, long n, double* out) {
   __shared__ double sh[32];
   double acc = 0;
@@ -171,10 +243,14 @@ __global__ void k_osj_finish(const zd* X, int m, int n, const zd* T, double tol,
   double* ws = w + m;
   int* perm = (int*)(ws + m);
   __shared__ int s_k;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    double acc = 0;
-    for (int j = 0; j < n; j++) acc += cabs2(X[(long)i * n + j]);
-    w[i] = acc;
+  {  // row norms, one warp per row
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i < m; i += nw) {
+      double acc = 0;
+      for (int j = lane; j < n; j += 32) acc += cabs2(X[(long)i * n + j]);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) w[i] = acc;
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -353,6 +429,16 @@ qlb_status svd_osj(qlb_ctx* ctx, zd* X, int m, int n, double tol, int cap, zd** 
   k_abs_thr<<<1, 256, 0, s>>>(X, (long)m * n, d_thr);
   int np = m + (m & 1);
   bool conv = (m <= 1);
+  if (!conv && (long)n <= 16384) {
+    // moderate rows: every sweep in one launch
+    int* d_sw = d_cnt;
+    k_osj_all<<<1, OSJ1_THREADS, 0, s>>>(X, m, n, T, d_thr, max_sweeps, d_sw);
+    int h_sw = 0;
+    cudaMemcpyAsync(&h_sw, d_sw, sizeof(int), cudaMemcpyDeviceToHost, s);
+    QLB_CUDA_TRY(cudaStreamSynchronize(s));
+    conv = h_sw > 0;
+    max_sweeps = 0;  // skip the multi-launch loop below
+  }
   for (int sw = 0; sw < max_sweeps && !conv; sw++) {
     cudaMemsetAsync(d_cnt, 0, sizeof(int), s);
     for (int r = 0; r < np - 1; r++) k_osj_round<<<np / 2, B_THREADS, 0, s>>>(X, m, n, T, np, r, d_cnt, d_thr);
