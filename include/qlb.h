@@ -186,6 +186,21 @@ qlb_status qlb_fidelity(qlb_state* st, const double* const* target_mode_vecs, do
 qlb_status qlb_trace(qlb_state* st, double* out);
 /* Tr rho^2 (Sec. IV.A). */
 qlb_status qlb_purity(qlb_state* st, double* out);
+/* Tr rho^2 like qlb_purity, but allocating no device memory.  The paper has no
+ * counterpart: this call exists for callers that must not allocate while they
+ * ask, e.g. code running inside CUDA stream capture (where cudaMalloc is not
+ * allowed), code whose device memory belongs to another allocator with a fixed
+ * budget, or monitoring loops that cannot pay for the device-wide
+ * synchronisation of cudaFree.  The Gram matrix and the sums live in a fixed
+ * scratch array inside the library's device image (about 256 KB, held by every
+ * GPU that loads the library until the process exits); it serves purification
+ * ranks chi_mu <= 128 and returns QLB_EINVAL with a message for larger ones.
+ * The first call on a device looks up that array's device address (no
+ * allocation); make that first call before any stream capture.  All calls share
+ * the one array, so calls that overlap on the GPU (other host threads, other
+ * streams) race; results are written, never accumulated, so a previous call's
+ * contents do not matter.  Synchronous; out receives the purity. */
+qlb_status qlb_purity_noalloc(qlb_state* st, double* out);
 /* [chi_mu, chi_1, ..., chi_{L-1}] (n_out = L). */
 qlb_status qlb_bond_dims(qlb_state* st, int* out, int cap, int* n_out);
 /* Diagnostics of the last step: out[0] = Tr rho before renormalisation,

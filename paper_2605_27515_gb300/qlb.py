@@ -73,6 +73,7 @@ _SIGS = {
     "qlb_fidelity": (_st, [_vp, C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.c_double)]),
     "qlb_trace": (_st, [_vp, C.POINTER(C.c_double)]),
     "qlb_purity": (_st, [_vp, C.POINTER(C.c_double)]),
+    "qlb_purity_noalloc": (_st, [_vp, C.POINTER(C.c_double)]),
     "qlb_bond_dims": (_st, [_vp, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
     "qlb_step_stats": (_st, [_vp, C.POINTER(C.c_double)]),
     "qlb_state_to_dense": (_st, [_vp, C.POINTER(C.c_double), C.c_size_t, C.POINTER(C.c_int)]),
@@ -299,6 +300,12 @@ class State:
     def purity(self) -> float:
         out = C.c_double()
         _check(self.lib.qlb_purity(self.h, C.byref(out)))
+        return out.value
+
+    def purity_noalloc(self) -> float:
+        """Tr rho^2 through the entry point that allocates no device memory."""
+        out = C.c_double()
+        _check(self.lib.qlb_purity_noalloc(self.h, C.byref(out)))
         return out.value
 
     def bond_dims(self):
