@@ -163,7 +163,7 @@ def run_gpu(args):
                   chi_mu_max=cfg["chi_mu_max"], stream_ordered=1)
     b = systems.build(ctx, cfg)
     st = b.sys.state(b.init)
-    stream = torch.cuda.ExternalStream(ctx.stream(), device=dev)
+    stream = torch.cuda.ExternalStream(st.stream(), device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
     dt = cfg["dt"]
     status = st.step(dt, args.warmup)
@@ -211,17 +211,20 @@ def run_gpu(args):
                 "launches": dp["launches"], "ms_per_launch": dp["ms"] / max(1, dp["launches"]),
                 "flops_per_launch": dp["flops"] / max(1, dp["launches"])}
 
-    # end to end through the public API: host vectors in, K steps, observables out
+    # end to end through the public API: host mode vector in (init), K steps each
+    # followed by a read-back of the photon number; the system's operators and
+    # Kraus MPO were built before (setup), as a caller stepping many states would
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st2 = b.sys.state(b.init)
-    st2.step(dt, args.warmup + args.steps)
-    n_obs = st2.expectation(b.observables["n"])
+    for _ in range(args.steps):
+        st2.step(dt, 1)
+        n_obs = st2.expectation(b.observables["n"])
     p_obs = st2.expectation(b.observables["parity"])
     e2e_s = time.perf_counter() - t0
-    e2e_steps = args.warmup + args.steps
+    e2e_steps = args.steps
     h2d = 16 * 512
-    d2h = 2 * 16
+    d2h = 16 * (args.steps + 1)
     st2.close()
 
     line = {
@@ -240,6 +243,8 @@ def run_gpu(args):
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "clocks": clk.summary(),
     }
+    if args.serving_requests > 0:
+        line["serving"] = serving_summary(dev, args.serving_requests, args.serving_step_scale, args.precision)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
     if rank == 0:
@@ -248,6 +253,26 @@ def run_gpu(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def serving_summary(dev, n_requests, step_scale, precision, budget_gb=4.0):
+    """The serving workload (Poisson arrivals at 200/s of single-cat requests,
+    seed 20260527) through the continuous-batching loop; step counts scaled by
+    step_scale so the run stays short.  Returns p50/p99 latency and steps/s."""
+    from paper_2605_27515_gb300 import inputs, qlb, serving
+
+    ctx = qlb.Ctx(device=dev, precision=precision, chi_max=64, chi_mu_max=8, stream_ordered=1)
+    reqs = inputs.serving_requests(n=n_requests)
+    srv = serving.Server(ctx, hbm_budget=int(budget_gb * (1 << 30)), max_slots=64, chunk=100)
+    t0 = time.perf_counter()
+    jobs = srv.run(reqs, step_scale=step_scale)
+    wall = time.perf_counter() - t0
+    out = serving.summarize(jobs, wall)
+    out.update({"workload": "serving", "step_scale": step_scale, "peak_live": srv.peak_live,
+                "peak_device_bytes": srv.peak_bytes, "hbm_budget_bytes": int(budget_gb * (1 << 30)),
+                "arrivals": "Poisson 200/s, seed 20260527"})
+    ctx.close()
+    return out
 
 
 def main():
@@ -259,6 +284,8 @@ def main():
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=32)
+    ap.add_argument("--serving-step-scale", type=float, default=0.005)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

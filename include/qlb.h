@@ -63,8 +63,9 @@ typedef struct qlb_state qlb_state;
 
 /* Arithmetic of the step. */
 #define QLB_PREC_F64 0   /* every operation in FP64 (the parity form) */
-#define QLB_PREC_MIXED 1 /* contractions and Gram matrices in FP32 split precision,
-                            truncation decisions and renormalisation in FP64 */
+#define QLB_PREC_MIXED 1 /* the Jacobi truncation solves in double-float (pairs of FP32,
+                            ~48-bit significands) on the FP32 pipes; contractions, Gram
+                            matrices, truncation decisions and renormalisation in FP64 */
 
 typedef struct {
   int device;            /* CUDA device ordinal */
@@ -74,7 +75,8 @@ typedef struct {
   int chi_max;           /* cap on every inter-site bond (default 64) */
   int chi_mu_max;        /* cap on the purification rank chi_mu (default 16) */
   double zip_tol_factor; /* the on-the-fly truncation inside the MPO application uses
-                            tol * zip_tol_factor (default 1e-2) */
+                            tol * zip_tol_factor (default 1e-6: the zip-up truncates in a
+                            frame that is not orthonormal, so it must cut far below tol) */
   double degeneracy_gap; /* singular values within this relative gap are one cluster and
                             are never split by a cut (default 1e-10) */
   int max_sweeps;        /* Jacobi sweep limit before QLB_ENOTCONV (default 40) */
@@ -92,9 +94,9 @@ void qlb_destroy(qlb_ctx* ctx);
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char* qlb_last_error(void);
 
-/* The cudaStream_t the context launches on (for callers that time with events). */
+/* The cudaStream_t the context runs its setup work on (operator builds). */
 qlb_status qlb_ctx_stream(qlb_ctx* ctx, void** stream);
-/* Waits for all work of the context. */
+/* Waits for all work of the context and of its states (device-wide). */
 qlb_status qlb_synchronize(qlb_ctx* ctx);
 /* Device bytes currently held by the context. */
 qlb_status qlb_ctx_memory(qlb_ctx* ctx, size_t* bytes);
@@ -139,7 +141,7 @@ typedef struct {
 /* Builds sum_t term_t as a quantics MPO (Sec. II.B): each term's per-mode dense
  * matrix is TT-SVD'd on the device into an MPO of R_m sites, the modes are
  * joined, the terms are summed and the sum is recompressed.  tol is the relative
- * discarded weight per bond (<= 0 selects 1e-26, i.e. only numerical zeros are
+ * discarded weight per bond (<= 0 selects 1e-30, i.e. only numerical zeros are
  * dropped); chi_max caps every MPO bond (<= 0: no cap).  The op keeps its dense
  * per-mode factors on the device so that L^dag L can be formed exactly. */
 qlb_status qlb_op_build(qlb_system* sys, const qlb_term* terms, int n_terms, double tol, int chi_max,
@@ -165,6 +167,14 @@ qlb_status qlb_add_jump(qlb_system* sys, const qlb_op* L);
  * holds N_m complex128 amplitudes (normalised by the call). */
 qlb_status qlb_state_init_product(qlb_system* sys, const double* const* mode_vecs, qlb_state** out);
 void qlb_state_destroy(qlb_state* st);
+/* The cudaStream_t of the state: every launch that touches the state (steps,
+ * observables) goes there, so states of one context step concurrently.  With
+ * stream_ordered set, callers time qlb_step with events on this stream. */
+qlb_status qlb_state_stream(qlb_state* st, void** stream);
+/* Non-blocking completion check of the state's enqueued work: QLB_OK when its
+ * stream is idle, 2 (a positive status, nothing done) while work is pending. */
+#define QLB_BUSY 2
+qlb_status qlb_state_poll(qlb_state* st);
 
 /* Sets the truncation parameters used by every later step of this state and
  * recompresses the state once with them (Sec. V.A compression, Sec. IV.A

@@ -124,6 +124,7 @@ qlb_op::~qlb_op() {
 }
 
 qlb_state::~qlb_state() {
+  if (stream) cudaStreamSynchronize(stream);
   if (graph) cudaGraphExecDestroy(graph);
   for (auto p : site) dev_free(nullptr, p);
   for (auto p : {X, Mb, G, Cin, Cout, T1, T2, T3, eigw}) dev_free(nullptr, p);
@@ -132,6 +133,7 @@ qlb_state::~qlb_state() {
   dev_free(nullptr, d_err);
   dev_free(nullptr, d_step);
   dev_free(nullptr, d_dims);
+  if (stream) cudaStreamDestroy(stream);
 }
 
 #define QLB_API extern "C" __attribute__((visibility("default")))
@@ -152,7 +154,7 @@ QLB_API void qlb_default_options(qlb_options* o) {
   o->tol = 1e-12;
   o->chi_max = 64;
   o->chi_mu_max = 16;
-  o->zip_tol_factor = 1e-2;
+  o->zip_tol_factor = 1e-6;
   o->degeneracy_gap = 1e-10;
   o->max_sweeps = 40;
   o->hbm_budget = 0;
@@ -174,7 +176,7 @@ QLB_API qlb_status qlb_create(const qlb_options* opt, qlb_ctx** out) {
   CHECK_ARG(o.chi_max >= 1 && o.chi_max <= 256, "chi_max must be in [1, 256]");
   CHECK_ARG(o.chi_mu_max >= 1 && o.chi_mu_max <= 128, "chi_mu_max must be in [1, 128]");
   CHECK_ARG(o.max_sweeps >= 1, "max_sweeps must be >= 1");
-  if (o.zip_tol_factor <= 0) o.zip_tol_factor = 1e-2;
+  if (o.zip_tol_factor <= 0) o.zip_tol_factor = 1e-6;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
     cudaGetLastError();
@@ -192,6 +194,13 @@ QLB_API qlb_status qlb_create(const qlb_options* opt, qlb_ctx** out) {
     return QLB_EDEVICE;
   }
   init_kernel_attributes();
+  // keep freed blocks in the device pool for reuse instead of returning them to
+  // the driver between allocations (process-local allocator setting)
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, o.device) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   *out = c;
   return QLB_OK;
 }
@@ -202,6 +211,10 @@ QLB_API void qlb_destroy(qlb_ctx* ctx) {
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   dev_free(ctx, ctx->d_prof);
   cudaStreamDestroy(ctx->stream);
+  // buffers still held by systems, ops or states of this context no longer
+  // report to it when they are freed later
+  for (auto& kv : g_alloc_sizes())
+    if (kv.second.second == ctx) kv.second.second = nullptr;
   delete ctx;
 }
 
@@ -211,9 +224,28 @@ QLB_API qlb_status qlb_ctx_stream(qlb_ctx* ctx, void** stream) {
   return QLB_OK;
 }
 
+QLB_API qlb_status qlb_state_stream(qlb_state* st, void** stream) {
+  CHECK_ARG(st && stream, "null argument");
+  *stream = (void*)st->stream;
+  return QLB_OK;
+}
+
+QLB_API qlb_status qlb_state_poll(qlb_state* st) {
+  CHECK_ARG(st, "null state");
+  cudaError_t e = cudaStreamQuery(st->stream);
+  if (e == cudaSuccess) return QLB_OK;
+  if (e == cudaErrorNotReady) {
+    cudaGetLastError();
+    return QLB_BUSY;
+  }
+  set_error(std::string("cudaStreamQuery: ") + cudaGetErrorString(e));
+  return QLB_EDEVICE;
+}
+
 QLB_API qlb_status qlb_synchronize(qlb_ctx* ctx) {
   CHECK_ARG(ctx, "null context");
   QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  QLB_CUDA_TRY(cudaDeviceSynchronize());
   return QLB_OK;
 }
 
@@ -242,6 +274,12 @@ QLB_API qlb_status qlb_system_create(qlb_ctx* ctx, int n_modes, const int* R, ql
   s->L = L;
   *out = s;
   return QLB_OK;
+}
+
+qlb_system::~qlb_system() { delete kraus_tmpl; }
+
+qlb_ctx::~qlb_ctx() {
+  for (auto& kv : factor_mpo_cache) delete kv.second;
 }
 
 QLB_API void qlb_system_destroy(qlb_system* sys) {
@@ -277,8 +315,9 @@ QLB_API qlb_status qlb_op_build(qlb_system* sys, const qlb_term* terms, int n_te
     DevTerm dt;
     dt.coeff = mk<double>(T.re, T.im);
     dt.fac.assign(sys->M, nullptr);
+    dt.key.assign(sys->M, "");
+    std::vector<bool> keyed(sys->M, true);
     double tb = std::sqrt(T.re * T.re + T.im * T.im);
-    std::vector<double> mode_norm(sys->M, 1.0);
     for (int f = 0; f < T.n_factors && !s; f++) {
       const qlb_factor& F = T.factors[f];
       if (F.mode < 0 || F.mode >= sys->M) {
@@ -315,8 +354,18 @@ QLB_API qlb_status qlb_op_build(qlb_system* sys, const qlb_term* terms, int n_te
         acc = nx;
       }
       dt.fac[F.mode] = acc;
+      if (F.kind == QLB_F_DENSE) {
+        keyed[F.mode] = false;
+      } else {
+        char piece[96];
+        snprintf(piece, sizeof(piece), "%s%d^%d@%.17g", dt.key[F.mode].empty() ? "" : "*", F.kind, p,
+                 F.kind == QLB_F_CHARGE ? F.param : 0.0);
+        dt.key[F.mode] += piece;
+      }
     }
     if (s) break;
+    for (int m = 0; m < sys->M; m++)
+      if (!keyed[m]) dt.key[m] = "";
     for (int m = 0; m < sys->M; m++)
       if (dt.fac[m]) tb *= dense_inf_norm(ctx, dt.fac[m], 1 << sys->R[m]);
     bound += tb;
@@ -438,7 +487,7 @@ QLB_API qlb_status qlb_state_to_dense(qlb_state* st, double* out, size_t n_doubl
   zd* T = nullptr;
   long rows = mu;
   if ((s = dev_alloc(ctx, (void**)&T, sizeof(zd) * mu * 2 * d[1]))) return s;
-  QLB_CUDA_TRY(cudaMemcpyAsync(T, st->site[0], sizeof(zd) * mu * 2 * d[1], cudaMemcpyDeviceToDevice, ctx->stream));
+  QLB_CUDA_TRY(cudaMemcpyAsync(T, st->site[0], sizeof(zd) * mu * 2 * d[1], cudaMemcpyDeviceToDevice, st->stream));
   rows *= 2;
   for (int i = 1; i < L; i++) {
     zd* nT = nullptr;
@@ -463,14 +512,14 @@ QLB_API qlb_status qlb_state_to_dense(qlb_state* st, double* out, size_t n_doubl
     g.m_max = (int)rows;
     g.n_max = (int)nn;
     g.nb_max = 1;
-    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, ctx->stream, nullptr));
+    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, st->stream, nullptr));
     dev_free(ctx, T);
     T = nT;
     rows *= 2;
   }
   std::vector<zd> h((size_t)mu * N);
-  QLB_CUDA_TRY(cudaMemcpyAsync(h.data(), T, sizeof(zd) * h.size(), cudaMemcpyDeviceToHost, ctx->stream));
-  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  QLB_CUDA_TRY(cudaMemcpyAsync(h.data(), T, sizeof(zd) * h.size(), cudaMemcpyDeviceToHost, st->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   dev_free(ctx, T);
   // h is [(mu, n)] ; out is [n][mu]
   for (int m = 0; m < mu; m++)
@@ -544,9 +593,14 @@ QLB_API qlb_status qlb_state_init_product(qlb_system* sys, const double* const* 
   for (int i = 0; i <= L; i++) hd[i] = D[i];
   for (int i = 0; i <= L; i++) hd[L + 1 + i] = D[i];
   QLB_CUDA_TRY(cudaMemcpy(st->d_dims, hd.data(), sizeof(int) * hd.size(), cudaMemcpyHostToDevice));
-  QLB_CUDA_TRY(cudaMemset(st->d_stats, 0, sizeof(double) * 8));
-  QLB_CUDA_TRY(cudaMemset(st->d_err, 0, sizeof(int) * 4));
-  QLB_CUDA_TRY(cudaMemset(st->d_step, 0, sizeof(long long)));
+  if (cudaStreamCreateWithFlags(&st->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    set_error("cudaStreamCreate failed");
+    delete st;
+    return QLB_EDEVICE;
+  }
+  QLB_CUDA_TRY(cudaMemsetAsync(st->d_stats, 0, sizeof(double) * 8, st->stream));
+  QLB_CUDA_TRY(cudaMemsetAsync(st->d_err, 0, sizeof(int) * 4, st->stream));
+  QLB_CUDA_TRY(cudaMemsetAsync(st->d_step, 0, sizeof(long long), st->stream));
   st->site = cores;
   cores.clear();
   st->site_cap.assign(L, 0);
@@ -561,7 +615,7 @@ QLB_API qlb_status qlb_state_init_product(qlb_system* sys, const double* const* 
 
 QLB_API void qlb_state_destroy(qlb_state* st) {
   if (!st) return;
-  cudaStreamSynchronize(st->sys->ctx->stream);
+  cudaStreamSynchronize(st->stream);
   delete st;
 }
 
@@ -613,6 +667,7 @@ QLB_API qlb_status qlb_fidelity(qlb_state* st, const double* const* target, doub
     if ((s = dev_alloc(ctx, (void**)&W.core[i], sizeof(zd) * n))) break;
     k_projector_core<<<nblk(n), 256, 0, ctx->stream>>>(P[i], D[i], D[i + 1], W.core[i]);
   }
+  cudaStreamSynchronize(ctx->stream);
   for (auto p : P) dev_free(ctx, p);
   double r[2] = {0, 0};
   if (!s) s = expectation_mpo(st, W, r);
@@ -655,11 +710,11 @@ QLB_API qlb_status qlb_purity(qlb_state* st, double* out) {
   g.alpha_re = 1;
   g.m_max = g.n_max = mu;
   g.nb_max = 1;
-  QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, ctx->stream, nullptr));
-  k_sum_abs2_n<<<1, 256, 0, ctx->stream>>>(G, (long)mu * mu, acc);
+  QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, st->stream, nullptr));
+  k_sum_abs2_n<<<1, 256, 0, st->stream>>>(G, (long)mu * mu, acc);
   double h = 0, tr = 0;
-  QLB_CUDA_TRY(cudaMemcpyAsync(&h, acc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  QLB_CUDA_TRY(cudaMemcpyAsync(&h, acc, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   dev_free(ctx, G);
   dev_free(ctx, acc);
   if ((s = state_sum_abs2_site0(st, &tr))) return s;
@@ -681,7 +736,7 @@ QLB_API qlb_status qlb_bond_dims(qlb_state* st, int* out, int cap, int* n_out) {
 QLB_API qlb_status qlb_step_stats(qlb_state* st, double* out4) {
   CHECK_ARG(st && out4, "null argument");
   double h[4];
-  QLB_CUDA_TRY(cudaStreamSynchronize(st->sys->ctx->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   QLB_CUDA_TRY(cudaMemcpy(h, st->d_stats, sizeof(h), cudaMemcpyDeviceToHost));
   long long steps = 0;
   QLB_CUDA_TRY(cudaMemcpy(&steps, st->d_step, sizeof(steps), cudaMemcpyDeviceToHost));
@@ -778,7 +833,7 @@ QLB_API qlb_status qlb_profile_enable(qlb_ctx* ctx, int on) {
 }
 
 static qlb_status prof_collect(qlb_ctx* ctx) {
-  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  QLB_CUDA_TRY(cudaDeviceSynchronize());
   for (auto& e : ctx->prof_events) {
     float ms = 0;
     QLB_CUDA_TRY(cudaEventElapsedTime(&ms, e.a, e.b));

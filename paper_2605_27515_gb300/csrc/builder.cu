@@ -25,10 +25,16 @@ qlb_status dev_alloc(qlb_ctx* ctx, void** p, size_t bytes) {
               std::to_string(ctx->opt.hbm_budget) + " bytes)");
     return QLB_ENOMEM;
   }
-  cudaError_t e = cudaMalloc(p, bytes);
+  // Stream-ordered allocation from the device's memory pool: unlike cudaMalloc /
+  // cudaFree it never synchronises the whole device, so admitting or retiring one
+  // state does not drain the steps other states have in flight.  The buffer is
+  // complete when the context stream is, which the synchronisation below ensures
+  // before any other stream touches it.
+  cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     *p = nullptr;
-    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    set_error(std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     return QLB_ENOMEM;
   }
   ctx->mem_held += bytes;
@@ -36,16 +42,22 @@ qlb_status dev_alloc(qlb_ctx* ctx, void** p, size_t bytes) {
   return QLB_OK;
 }
 
+// Returns p to the pool in the order of its owner's stream (every caller has
+// synchronised the streams that used p); without a live owner, plain cudaFree.
 void dev_free(qlb_ctx*, void* p) {
   if (!p) return;
   auto& m = g_alloc_sizes();
   auto it = m.find(p);
+  qlb_ctx* owner = nullptr;
   if (it != m.end()) {
-    qlb_ctx* owner = it->second.second;
+    owner = it->second.second;
     if (owner) owner->mem_held -= std::min(owner->mem_held, it->second.first);
     m.erase(it);
   }
-  cudaFree(p);
+  if (owner && owner->stream)
+    cudaFreeAsync(p, owner->stream);
+  else
+    cudaFree(p);
 }
 
 std::map<void*, std::pair<size_t, qlb_ctx*>>& g_alloc_sizes() {
@@ -768,10 +780,26 @@ qlb_status mpo_from_terms(qlb_system* sys, const std::vector<DevTerm>& terms, do
     Mpo term;
     for (int m = 0; m < sys->M; m++) {
       Mpo part;
-      if (terms[t].fac[m])
+      const std::string key = (terms[t].fac[m] && m < (int)terms[t].key.size() && !terms[t].key[m].empty())
+                                  ? std::to_string(sys->R[m]) + "|" + terms[t].key[m]
+                                  : std::string();
+      auto hit = key.empty() ? ctx->factor_mpo_cache.end() : ctx->factor_mpo_cache.find(key);
+      if (hit != ctx->factor_mpo_cache.end()) {
+        st = mpo_copy(ctx, *hit->second, part);
+      } else if (terms[t].fac[m]) {
         st = mpo_from_dense(ctx, terms[t].fac[m], sys->R[m], 1e-32, 0, part);
-      else
+        if (!st && !key.empty()) {
+          // keep a copy: the same built-in factor on the same R gives the same MPO
+          Mpo* c = new Mpo();
+          st = mpo_copy(ctx, part, *c);
+          if (st)
+            delete c;
+          else
+            ctx->factor_mpo_cache[key] = c;
+        }
+      } else {
         st = make_identity_mpo(ctx, sys->R[m], part);
+      }
       if (st) {
         mpo_clear(ctx, term);
         mpo_clear(ctx, part);

@@ -134,12 +134,12 @@ QLB_API qlb_status qlb_purity_noalloc(qlb_state* st, double* out) {
   g.alpha_re = 1;
   g.m_max = g.n_max = mu;
   g.nb_max = 1;
-  QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, ctx->stream, nullptr));
-  k_purity_reduce<<<1, 256, 0, ctx->stream>>>(G, mu, st->site[0], (long)mu * 2 * r, res);
+  QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, st->stream, nullptr));
+  k_purity_reduce<<<1, 256, 0, st->stream>>>(G, mu, st->site[0], (long)mu * 2 * r, res);
   QLB_CUDA_TRY(cudaGetLastError());
   double h[2] = {0, 0};
-  QLB_CUDA_TRY(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
-  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  QLB_CUDA_TRY(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   *out = h[1] > 0 ? h[0] / (h[1] * h[1]) : 0.0;
   return QLB_OK;
 }

@@ -1,6 +1,7 @@
 // Object model behind the opaque C-ABI handles.
 #pragma once
 
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -8,6 +9,8 @@
 #include "qlb_internal.cuh"
 
 namespace qlb {
+
+struct Kraus;
 
 // ------------------------------------------------------------------ device buffers
 
@@ -35,6 +38,10 @@ struct Mpo {
 struct DevTerm {
   zd coeff;
   std::vector<zd*> fac;  // one per mode; owned by the op (shared_ptr-free: freed with the op)
+  // per mode, a recipe naming the factor when it is made of built-in factors only
+  // ("" for caller matrices); equal recipes on equal R give equal matrices, so
+  // their MPOs are cached by the context
+  std::vector<std::string> key;
 };
 
 }  // namespace qlb
@@ -55,6 +62,9 @@ struct qlb_ctx {
   double* d_prof = nullptr;  // [QLB_K_COUNT] flops, [QLB_K_COUNT..2*] bytes
   double prof_ms[QLB_K_COUNT] = {0};
   long long prof_launch[QLB_K_COUNT] = {0};
+  // MPOs of built-in per-mode factors, keyed by "R|recipe" (see DevTerm::key)
+  std::map<std::string, qlb::Mpo*> factor_mpo_cache;
+  ~qlb_ctx();
 };
 
 struct qlb_system {
@@ -69,6 +79,10 @@ struct qlb_system {
   int64_t n_f = 0;
   std::vector<const qlb_op*> jumps;
   int version = 0;  // bumped when H or jumps change
+  // Kraus MPO of the last (dt, version) built by any state of this system; new
+  // states copy it instead of rebuilding (owned, freed with the system)
+  qlb::Kraus* kraus_tmpl = nullptr;
+  ~qlb_system();
 };
 
 struct qlb_op {
@@ -108,6 +122,9 @@ struct qlb_state {
   double tol = 1e-12;
   int chi_max = 64, chi_mu_max = 16;
   int cap_chi = 64, cap_mu = 16;  // allocation caps
+  // every launch that touches this state goes to its own stream, so independent
+  // states step concurrently on the GPU; setup work stays on the context stream
+  cudaStream_t stream = nullptr;
   // device dims: [0..L] state bonds, [L+1 .. 2L+1] zip-up bonds
   int* d_dims = nullptr;
   std::vector<int> cap_state;  // host capacities of state bonds [0..L]

@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "df64.cuh"
 #include "step.cuh"
 
 namespace qlb {
@@ -145,7 +146,7 @@ __global__ void k_identity_core(zd* W) {
 
 // ------------------------------------------------------------------ launch helpers
 
-static void prof_before(qlb_ctx* ctx, int kclass, cudaEvent_t* a) {
+static void prof_before(qlb_ctx* ctx, cudaStream_t sm, int kclass, cudaEvent_t* a) {
   *a = nullptr;
   if (!ctx->prof_on) return;
   if (ctx->ev_used + 2 > ctx->ev_pool.size()) {
@@ -156,13 +157,13 @@ static void prof_before(qlb_ctx* ctx, int kclass, cudaEvent_t* a) {
     }
   }
   *a = ctx->ev_pool[ctx->ev_used++];
-  cudaEventRecord(*a, ctx->stream);
+  cudaEventRecord(*a, sm);
   (void)kclass;
 }
-static void prof_after(qlb_ctx* ctx, int kclass, cudaEvent_t a) {
+static void prof_after(qlb_ctx* ctx, cudaStream_t sm, int kclass, cudaEvent_t a) {
   if (!ctx->prof_on || !a) return;
   cudaEvent_t b = ctx->ev_pool[ctx->ev_used++];
-  cudaEventRecord(b, ctx->stream);
+  cudaEventRecord(b, sm);
   ctx->prof_events.push_back({kclass, a, b});
 }
 
@@ -182,9 +183,9 @@ static void debug_dump(qlb_state* st, int tag, const void* out) {
   FILE* f = debug_file();
   if (!f) return;
   cudaStreamCaptureStatus cs;
-  cudaStreamIsCapturing(st->sys->ctx->stream, &cs);
+  cudaStreamIsCapturing(st->stream, &cs);
   if (cs != cudaStreamCaptureStatusNone) return;
-  cudaStreamSynchronize(st->sys->ctx->stream);
+  cudaStreamSynchronize(st->stream);
   int n = 2 * st->L + 2;
   std::vector<int> d(n);
   cudaMemcpy(d.data(), st->d_dims, sizeof(int) * n, cudaMemcpyDeviceToHost);
@@ -202,9 +203,9 @@ static void debug_dump(qlb_state* st, int tag, const void* out) {
 static qlb_status gemm(qlb_state* st, GemmDesc& g) {
   qlb_ctx* ctx = st->sys->ctx;
   cudaEvent_t a;
-  prof_before(ctx, g.kclass, &a);
-  cudaError_t e = launch_gemm<double>(g, st->d_dims, ctx->stream, ctx->prof_on ? ctx->d_prof + g.kclass : nullptr);
-  prof_after(ctx, g.kclass, a);
+  prof_before(ctx, st->stream, g.kclass, &a);
+  cudaError_t e = launch_gemm<double>(g, st->d_dims, st->stream, ctx->prof_on ? ctx->d_prof + g.kclass : nullptr);
+  prof_after(ctx, st->stream, g.kclass, a);
   if (e != cudaSuccess) {
     set_error(std::string("gemm launch: ") + cudaGetErrorString(e));
     return QLB_EDEVICE;
@@ -216,9 +217,12 @@ static qlb_status gemm(qlb_state* st, GemmDesc& g) {
 static qlb_status eig(qlb_state* st, EigDesc& e) {
   qlb_ctx* ctx = st->sys->ctx;
   cudaEvent_t a;
-  prof_before(ctx, QLB_K_EIG, &a);
-  cudaError_t r = launch_eig<double>(e, st->d_dims, ctx->stream, st->eigw, ctx->prof_on ? ctx->d_prof + QLB_K_EIG : nullptr);
-  prof_after(ctx, QLB_K_EIG, a);
+  prof_before(ctx, st->stream, QLB_K_EIG, &a);
+  double* pf = ctx->prof_on ? ctx->d_prof + QLB_K_EIG : nullptr;
+  // the mixed form runs the same Jacobi in double-float on the FP32 pipes
+  cudaError_t r = st->prec == QLB_PREC_MIXED ? launch_eig<df64>(e, st->d_dims, st->stream, st->eigw, pf)
+                                             : launch_eig<double>(e, st->d_dims, st->stream, st->eigw, pf);
+  prof_after(ctx, st->stream, QLB_K_EIG, a);
   if (r != cudaSuccess) {
     set_error(std::string("eig launch: ") + cudaGetErrorString(r));
     return QLB_EDEVICE;
@@ -230,9 +234,9 @@ static qlb_status eig(qlb_state* st, EigDesc& e) {
 static qlb_status copy(qlb_state* st, zd* dst, const zd* src, DimExpr cnt, long max_n) {
   qlb_ctx* ctx = st->sys->ctx;
   cudaEvent_t a;
-  prof_before(ctx, QLB_K_OTHER, &a);
-  k_copy<<<nblk(max_n), 256, 0, ctx->stream>>>(dst, src, cnt, st->d_dims);
-  prof_after(ctx, QLB_K_OTHER, a);
+  prof_before(ctx, st->stream, QLB_K_OTHER, &a);
+  k_copy<<<nblk(max_n), 256, 0, st->stream>>>(dst, src, cnt, st->d_dims);
+  prof_after(ctx, st->stream, QLB_K_OTHER, a);
   QLB_CUDA_TRY(cudaGetLastError());
   return QLB_OK;
 }
@@ -306,6 +310,37 @@ qlb_status build_identity_kraus(qlb_state* st) {
 // stacked with branch k on the left boundary and jointly recompressed.  With a
 // drive the H1 block is appended uncompressed on branch 0 and its core 0 is
 // rewritten every step with -i h f(t_n).
+// Device copy of a Kraus MPO (each state owns its copy: the drive rewrites core 0).
+static qlb_status kraus_copy(qlb_ctx* ctx, const Kraus& src, Kraus& dst) {
+  kraus_clear(ctx, dst);
+  dst.dt = src.dt;
+  dst.version = src.version;
+  dst.B = src.B;
+  dst.L = src.L;
+  dst.D = src.D;
+  dst.driven = src.driven;
+  dst.drive_off = src.drive_off;
+  dst.drive_D1 = src.drive_D1;
+  dst.unstable_factor = src.unstable_factor;
+  dst.W.assign(src.L, nullptr);
+  for (int i = 0; i < src.L; i++) {
+    size_t b = sizeof(zd) * (size_t)src.D[i] * 4 * src.D[i + 1];
+    qlb_status s = dev_alloc(ctx, (void**)&dst.W[i], b);
+    if (s) return s;
+    QLB_CUDA_TRY(cudaMemcpyAsync(dst.W[i], src.W[i], b, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  if (src.drive_core0) {
+    size_t b = sizeof(zd) * 4 * (size_t)src.drive_D1;
+    qlb_status s = dev_alloc(ctx, (void**)&dst.drive_core0, b);
+    if (s) return s;
+    QLB_CUDA_TRY(cudaMemcpyAsync(dst.drive_core0, src.drive_core0, b, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return QLB_OK;
+}
+
+static qlb_status build_kraus_fresh(qlb_state* st, double dt);
+
 qlb_status build_kraus(qlb_state* st, double dt) {
   qlb_system* sys = st->sys;
   qlb_ctx* ctx = sys->ctx;
@@ -314,6 +349,17 @@ qlb_status build_kraus(qlb_state* st, double dt) {
     set_error("system has neither a Hamiltonian nor jump operators");
     return QLB_ESTATE;
   }
+  Kraus* t = sys->kraus_tmpl;
+  if (t && t->dt == dt && t->version == sys->version) return kraus_copy(ctx, *t, st->kraus);
+  qlb_status s = build_kraus_fresh(st, dt);
+  if (s) return s;
+  if (!t) t = sys->kraus_tmpl = new Kraus();
+  return kraus_copy(ctx, st->kraus, *t);
+}
+
+static qlb_status build_kraus_fresh(qlb_state* st, double dt) {
+  qlb_system* sys = st->sys;
+  qlb_ctx* ctx = sys->ctx;
   kraus_clear(ctx, st->kraus);
   qlb_status s;
   // U_1 terms
@@ -322,6 +368,7 @@ qlb_status build_kraus(qlb_state* st, double dt) {
   DevTerm id;
   id.coeff = mk<double>(1.0, 0.0);
   id.fac.assign(sys->M, nullptr);
+  id.key.assign(sys->M, "");
   terms.push_back(id);
   if (sys->H0)
     for (auto& t : sys->H0->terms) {
@@ -339,11 +386,16 @@ qlb_status build_kraus(qlb_state* st, double dt) {
         u.coeff = cmul(cconj(ta.coeff), tb.coeff);
         u.coeff = cscale(u.coeff, -0.5 * dt);  // -i h * (-i/2) = -h/2
         u.fac.assign(sys->M, nullptr);
+        u.key.assign(sys->M, "");
         for (int m = 0; m < sys->M; m++) {
           int N = 1 << sys->R[m];
           const zd* A = ta.fac[m];
           const zd* B = tb.fac[m];
           if (!A && !B) continue;
+          const std::string& ka = ta.key[m];
+          const std::string& kb = tb.key[m];
+          if ((!A || !ka.empty()) && (!B || !kb.empty()))
+            u.key[m] = (A ? "dag(" + ka + ")" : std::string()) + (A && B ? "*" : "") + (B ? "(" + kb + ")" : "");
           zd* P = nullptr;
           if (A && B)
             s = dense_mul(ctx, A, OP_C, B, N, &P);
@@ -526,7 +578,7 @@ qlb_status plan_buffers(qlb_state* st, const Kraus& K) {
       if ((s = dev_alloc(ctx, (void**)&p, sizeof(zd) * need))) return s;
       size_t have = (size_t)cur[i] * 2 * cur[i + 1];
       if (st->site[i] && have)
-        QLB_CUDA_TRY(cudaMemcpyAsync(p, st->site[i], sizeof(zd) * have, cudaMemcpyDeviceToDevice, ctx->stream));
+        QLB_CUDA_TRY(cudaMemcpyAsync(p, st->site[i], sizeof(zd) * have, cudaMemcpyDeviceToDevice, st->stream));
       dev_free(ctx, st->site[i]);
       st->site[i] = p;
       st->site_cap[i] = need;
@@ -537,7 +589,7 @@ qlb_status plan_buffers(qlb_state* st, const Kraus& K) {
     for (size_t j = 0; j < c.hd.size(); j++) c.hd[j] = std::max(c.hd[j], st->cap_state[j]);
   st->cap_state = c.hd;
   st->plan_key++;
-  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   return QLB_OK;
 }
 
@@ -677,12 +729,12 @@ qlb_status enqueue_step(qlb_state* st, const Kraus& K, bool count_step) {
   qlb_status s;
   {
     cudaEvent_t a;
-    prof_before(ctx, QLB_K_OTHER, &a);
+    prof_before(ctx, st->stream, QLB_K_OTHER, &a);
     long n0 = (long)cap(ZB(st, 0)) * cap(SB(0)) * K.B;
-    k_step_begin<<<nblk(n0), 256, 0, ctx->stream>>>(
+    k_step_begin<<<nblk(n0), 256, 0, st->stream>>>(
         st->d_dims, L, K.B, st->Cin, (long)st->nC, K.driven ? K.W[0] : nullptr, K.driven ? K.drive_core0 : nullptr,
         K.D[1], K.drive_off, K.drive_D1, st->sys->d_f, st->sys->n_f, st->d_step, K.dt, st->d_stats);
-    prof_after(ctx, QLB_K_OTHER, a);
+    prof_after(ctx, st->stream, QLB_K_OTHER, a);
     QLB_CUDA_TRY(cudaGetLastError());
   }
   zd* Cin = st->Cin;
@@ -781,9 +833,9 @@ qlb_status enqueue_step(qlb_state* st, const Kraus& K, bool count_step) {
   if ((s = enqueue_compress(st, hd))) return s;
   {
     cudaEvent_t a;
-    prof_before(ctx, QLB_K_OTHER, &a);
-    k_step_end<<<1, 32, 0, ctx->stream>>>(st->d_step, count_step ? 1 : 0);
-    prof_after(ctx, QLB_K_OTHER, a);
+    prof_before(ctx, st->stream, QLB_K_OTHER, &a);
+    k_step_end<<<1, 32, 0, st->stream>>>(st->d_step, count_step ? 1 : 0);
+    prof_after(ctx, st->stream, QLB_K_OTHER, a);
     QLB_CUDA_TRY(cudaGetLastError());
   }
   return QLB_OK;
@@ -792,8 +844,8 @@ qlb_status enqueue_step(qlb_state* st, const Kraus& K, bool count_step) {
 qlb_status read_dims(qlb_state* st, std::vector<int>& d) {
   qlb_ctx* ctx = st->sys->ctx;
   d.assign(2 * st->L + 2, 0);
-  QLB_CUDA_TRY(cudaMemcpyAsync(d.data(), st->d_dims, sizeof(int) * d.size(), cudaMemcpyDeviceToHost, ctx->stream));
-  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  QLB_CUDA_TRY(cudaMemcpyAsync(d.data(), st->d_dims, sizeof(int) * d.size(), cudaMemcpyDeviceToHost, st->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   return QLB_OK;
 }
 
@@ -809,9 +861,9 @@ qlb_status run_steps(qlb_state* st, int64_t n, bool sync) {
       if (st->graph) cudaGraphExecDestroy(st->graph);
       st->graph = nullptr;
       cudaGraph_t gr;
-      QLB_CUDA_TRY(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      QLB_CUDA_TRY(cudaStreamBeginCapture(st->stream, cudaStreamCaptureModeThreadLocal));
       s = enqueue_step(st, st->kraus, true);
-      cudaError_t e = cudaStreamEndCapture(ctx->stream, &gr);
+      cudaError_t e = cudaStreamEndCapture(st->stream, &gr);
       if (s) {
         if (e == cudaSuccess) cudaGraphDestroy(gr);
         return s;
@@ -822,11 +874,11 @@ qlb_status run_steps(qlb_state* st, int64_t n, bool sync) {
       QLB_CUDA_TRY(e);
       st->graph_key = st->plan_key;
     }
-    for (int64_t k = 0; k < n; k++) QLB_CUDA_TRY(cudaGraphLaunch(st->graph, ctx->stream));
+    for (int64_t k = 0; k < n; k++) QLB_CUDA_TRY(cudaGraphLaunch(st->graph, st->stream));
   }
   st->host_steps += n;
   if (!sync) return QLB_OK;
-  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   int err = 0;
   QLB_CUDA_TRY(cudaMemcpy(&err, st->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (err) {
@@ -854,7 +906,7 @@ qlb_status truncate_pass(qlb_state* st) {
   if ((s = plan_buffers(st, st->kraus_id))) return s;
   if ((s = enqueue_step(st, st->kraus_id, false))) return s;
   qlb_ctx* ctx = st->sys->ctx;
-  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   int err = 0;
   QLB_CUDA_TRY(cudaMemcpy(&err, st->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (err) {
@@ -891,7 +943,7 @@ qlb_status expectation_mpo(qlb_state* st, const Mpo& Wb, double* out) {
       cleanup();
       return s;
     }
-    k_to_step_layout<<<nblk(n), 256, 0, ctx->stream>>>(Wb.core[i], Wb.D[i], Wb.D[i + 1], W[i]);
+    k_to_step_layout<<<nblk(n), 256, 0, st->stream>>>(Wb.core[i], Wb.D[i], Wb.D[i + 1], W[i]);
   }
   size_t nE = 1, nY = 1, nZ = 1;
   for (int i = 0; i < L; i++) {
@@ -911,8 +963,8 @@ qlb_status expectation_mpo(qlb_state* st, const Mpo& Wb, double* out) {
   {
     std::vector<zd> h((size_t)d[0] * d[0], mk<double>(0, 0));
     for (int m = 0; m < d[0]; m++) h[(size_t)m * d[0] + m] = mk<double>(1, 0);
-    QLB_CUDA_TRY(cudaMemcpyAsync(E0, h.data(), sizeof(zd) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
-    QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    QLB_CUDA_TRY(cudaMemcpyAsync(E0, h.data(), sizeof(zd) * h.size(), cudaMemcpyHostToDevice, st->stream));
+    QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   }
   for (int i = 0; i < L; i++) {
     int l = d[i], r = d[i + 1], Dl = Wb.D[i], Dr = Wb.D[i + 1];
@@ -933,7 +985,7 @@ qlb_status expectation_mpo(qlb_state* st, const Mpo& Wb, double* out) {
     g.m_max = Dl;
     g.n_max = 2 * r;
     g.nb_max = l;
-    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, ctx->stream, nullptr));
+    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, st->stream, nullptr));
     g = gdesc();
     g.A = Y;
     g.B = W[i];
@@ -954,7 +1006,7 @@ qlb_status expectation_mpo(qlb_state* st, const Mpo& Wb, double* out) {
     g.m_max = r;
     g.n_max = Dr;
     g.nb_max = 2 * l;
-    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, ctx->stream, nullptr));
+    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, st->stream, nullptr));
     g = gdesc();
     g.A = st->site[i];
     g.B = Z;
@@ -968,12 +1020,12 @@ qlb_status expectation_mpo(qlb_state* st, const Mpo& Wb, double* out) {
     g.ldc = dconst(r * Dr);
     g.m_max = r;
     g.n_max = r * Dr;
-    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, ctx->stream, nullptr));
+    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, st->stream, nullptr));
     std::swap(E0, E1);
   }
   zd res;
-  QLB_CUDA_TRY(cudaMemcpyAsync(&res, E0, sizeof(zd), cudaMemcpyDeviceToHost, ctx->stream));
-  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  QLB_CUDA_TRY(cudaMemcpyAsync(&res, E0, sizeof(zd), cudaMemcpyDeviceToHost, st->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   cleanup();
   out[0] = res.re;
   out[1] = res.im;
@@ -990,7 +1042,7 @@ qlb_status kraus_branch(qlb_state* st, int k, Mpo& out) {
     return QLB_EINVAL;
   }
   if (K.driven)
-    k_drive_rewrite<<<1, 256, 0, ctx->stream>>>(K.W[0], K.drive_core0, K.B, K.D[1], K.drive_off, K.drive_D1,
+    k_drive_rewrite<<<1, 256, 0, st->stream>>>(K.W[0], K.drive_core0, K.B, K.D[1], K.drive_off, K.drive_D1,
                                                 st->sys->d_f, st->sys->n_f, st->d_step, K.dt);
   mpo_clear(ctx, out);
   out.L = K.L;
@@ -1001,18 +1053,19 @@ qlb_status kraus_branch(qlb_state* st, int k, Mpo& out) {
     long n = (long)out.D[i] * 4 * out.D[i + 1];
     qlb_status s = dev_alloc(ctx, (void**)&out.core[i], sizeof(zd) * n);
     if (s) return s;
-    k_from_step_layout<<<nblk(n), 256, 0, ctx->stream>>>(K.W[i], K.D[i], K.D[i + 1], i == 0 ? k : -1, out.core[i]);
+    k_from_step_layout<<<nblk(n), 256, 0, st->stream>>>(K.W[i], K.D[i], K.D[i + 1], i == 0 ? k : -1, out.core[i]);
   }
   QLB_CUDA_TRY(cudaGetLastError());
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   return QLB_OK;
 }
 
 qlb_status state_sum_abs2_site0(qlb_state* st, double* out) {
   qlb_ctx* ctx = st->sys->ctx;
   double* d = st->d_stats + 3;
-  k_sum_abs2<<<1, 256, 0, ctx->stream>>>(st->site[0], dvar2(SB(0), SB(1), 2), st->d_dims, d);
-  QLB_CUDA_TRY(cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  QLB_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  k_sum_abs2<<<1, 256, 0, st->stream>>>(st->site[0], dvar2(SB(0), SB(1), 2), st->d_dims, d);
+  QLB_CUDA_TRY(cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+  QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
   return QLB_OK;
 }
 

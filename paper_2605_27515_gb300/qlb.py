@@ -56,6 +56,8 @@ _SIGS = {
     "qlb_last_error": (C.c_char_p, []),
     "qlb_ctx_stream": (_st, [_vp, C.POINTER(_vp)]),
     "qlb_synchronize": (_st, [_vp]),
+    "qlb_state_stream": (_st, [_vp, C.POINTER(_vp)]),
+    "qlb_state_poll": (_st, [_vp]),
     "qlb_ctx_memory": (_st, [_vp, C.POINTER(C.c_size_t)]),
     "qlb_system_create": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "qlb_system_destroy": (None, [_vp]),
@@ -276,6 +278,15 @@ class State:
 
     def step(self, dt, n=1) -> int:
         return _check(self.lib.qlb_step(self.h, float(dt), int(n)))
+
+    def stream(self) -> int:
+        s = _vp()
+        _check(self.lib.qlb_state_stream(self.h, C.byref(s)))
+        return s.value or 0
+
+    def poll(self) -> bool:
+        """True when the state's enqueued work has finished."""
+        return _check(self.lib.qlb_state_poll(self.h)) == OK
 
     def truncate(self, tol=0.0, chi_max=0, chi_mu_max=0):
         return _check(self.lib.qlb_truncate(self.h, float(tol), int(chi_max), int(chi_mu_max)))

@@ -1,0 +1,75 @@
+"""GPU parity of the model systems at the oracle's check sizes (truncated form).
+
+Bar: photon numbers, parities and other recorded observables within 1e-6
+absolute of the dense FP64 oracle (the truncated-form tolerance).
+
+* large cat mode at its check size N = 128, alpha^2 = 16, Zeno drive, literal
+  dt = 5e-4 (recorded before the explicit step's instability takes over, and the
+  stable twin dt = 1e-4 over a longer window);
+* transmon x resonator at 32 charge states x 64 Fock levels with the ramped drive;
+* the two coupled cats with buffers at (N_b, N_a, N_a, N_b) = (4, 8, 8, 4).
+"""
+import numpy as np
+import pytest
+
+from oracle import dense as D
+from oracle import systems as OS
+from paper_2605_27515_gb300 import inputs
+from paper_2605_27515_gb300 import qlb as Q
+from paper_2605_27515_gb300 import systems
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare(b, ds, dt, nsteps, every, names):
+    st = b.sys.state(b.init)
+    _, recs = ds.evolve(dt, nsteps, every, names=names)
+    worst = {n: 0.0 for n in names}
+    done = 0
+    for step, vals in recs[1:]:
+        st.step(dt, step - done)
+        done = step
+        for n, o in zip(names, vals):
+            g = st.expectation(b.observables[n]).real
+            worst[n] = max(worst[n], abs(g - o))
+    st.close()
+    return worst
+
+
+@pytest.mark.parametrize("dt,nsteps,zipf", [(5e-4, 100, 1e-2), (1e-4, 600, 1e-2), (1e-4, 600, 1e-6)])
+def test_cat_r9_check_size(dt, nsteps, zipf):
+    cfg = inputs.config("cat_r9")
+    cfg.update(cfg.pop("check"))  # N = 128, alpha^2 = 16
+    c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"], zip_tol_factor=zipf)
+    b = systems.build(c, cfg)
+    worst = _compare(b, OS.cat(cfg), dt, nsteps, 20, ["n", "parity"])
+    assert max(worst.values()) < 1e-6, worst
+    c.close()
+
+
+def test_transmon_check_size():
+    cfg = inputs.config("transmon")
+    cfg.update(cfg.pop("check"))  # 32 charge states x 64 Fock levels
+    nsteps = 20
+    dt = 2e-5
+    cfg["dt"] = dt
+    c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])
+    b = systems.build(c, cfg, nsteps=nsteps)
+    Nt = 2 ** cfg["R"][0]
+    init = [inputs.transmon_ground_charge(Nt, Nt // 2, cfg["ec"], cfg["ej_over_ec"] * cfg["ec"]),
+            D.fock(2 ** cfg["R"][1], 0)]
+    ds = OS.transmon(cfg, nsteps, b.f_table, init)
+    worst = _compare(b, ds, dt, nsteps, 5, ["n_c", "n_t2"])
+    assert max(worst.values()) < 1e-6, worst
+    c.close()
+
+
+def test_cat_pair_check_size():
+    cfg = inputs.config("cat_pair")
+    cfg.update(cfg.pop("check"))  # R = [3, 2, 3, 2] -> modes [4, 8, 8, 4]
+    dt = 2e-3
+    c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])
+    b = systems.build(c, cfg)
+    worst = _compare(b, OS.cat_pair(cfg), dt, 60, 20, ["n_a1", "n_a2", "parity_a1"])
+    assert max(worst.values()) < 1e-6, worst
+    c.close()
