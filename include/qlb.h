@@ -160,6 +160,17 @@ qlb_status qlb_set_hamiltonian(qlb_system* sys, const qlb_op* H0, const qlb_op* 
                                int64_t n_f);
 /* Adds a Lindblad operator L_k (Eq. 1).  Referenced, not copied. */
 qlb_status qlb_add_jump(qlb_system* sys, const qlb_op* L);
+/* Selects the Kraus scheme used by qlb_step (Sec. V.B).
+ *   order 1 (default): K = U + h L, Kraus operators U_1 = 1 - i h H_eff and
+ *     sqrt(h) L_k, local error O(h^2).
+ *   order 2: K = U' + (h/2)(U L + L U) + (h^2/2) L^2, Kraus operators
+ *     U_1' = 1 - i h H_eff - (h^2/2) H_eff^2, sqrt(h/2) U_1 L_k, sqrt(h/2) L_k U_1
+ *     and (h/sqrt 2) L_j L_k: 1 + 2l + l^2 branches on the purification leg,
+ *     local error O(h^3).
+ * Order 2 needs a time-independent Hamiltonian (H1 == NULL) and at most 6 jump
+ * operators; otherwise QLB_EINVAL (here, or from qlb_step if the system changes
+ * afterwards).  States rebuild their Kraus MPO on their next step. */
+qlb_status qlb_set_scheme(qlb_system* sys, int order);
 
 /* ------------------------------------------------------------------ states */
 

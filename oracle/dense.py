@@ -174,12 +174,34 @@ def sandwich(A: Operator, rho: np.ndarray) -> np.ndarray:
     return A.apply_left(X.conj().T)
 
 
-def kraus_step(rho: np.ndarray, H: Operator, Ls, h: float, normalize: bool = True) -> np.ndarray:
-    """One first-order Kraus step K = U + h L (Sec. V.B), then rho / Tr rho."""
-    U = u1(H, Ls, h)
-    out = sandwich(U, rho)
-    for L in Ls:
-        out = out + h * sandwich(L, rho)
+def kraus_step(rho: np.ndarray, H: Operator, Ls, h: float, normalize: bool = True, order: int = 1) -> np.ndarray:
+    """One Kraus step, then rho / Tr rho (Sec. V.B).
+
+    order 1: K = U + h L with U(rho) = U_1 rho U_1^dag.
+    order 2: K = U' + (h/2)(U L + L U) + (h^2/2) L^2 with U'(rho) = U_1' rho U_1'^dag,
+             U_1' = 1 - i h H_eff - (h^2/2) H_eff^2; the compositions of Kraus maps
+             are applied one after the other (Sec. V.B, Kraus algebra)."""
+    if order == 1:
+        U = u1(H, Ls, h)
+        out = sandwich(U, rho)
+        for L in Ls:
+            out = out + h * sandwich(L, rho)
+    elif order == 2:
+        He = h_eff(H, Ls)
+        U = u1(H, Ls, h)
+        Up = U + (He @ He).scale(-0.5 * h * h)
+
+        def jump(r):
+            acc = np.zeros_like(r)
+            for L in Ls:
+                acc = acc + sandwich(L, r)
+            return acc
+
+        out = sandwich(Up, rho)
+        out = out + (h / 2) * (sandwich(U, jump(rho)) + jump(sandwich(U, rho)))
+        out = out + (h * h / 2) * jump(jump(rho))
+    else:
+        raise ValueError("order must be 1 or 2")
     out = 0.5 * (out + out.conj().T)  # exact Hermiticity; removes rounding skew only
     if normalize:
         out = out / np.trace(out).real
@@ -187,11 +209,12 @@ def kraus_step(rho: np.ndarray, H: Operator, Ls, h: float, normalize: bool = Tru
 
 
 def evolve(rho0, H0: Operator, Ls, h: float, nsteps: int, H1: Operator | None = None, f_table=None,
-           record_every: int = 0, observables=None):
+           record_every: int = 0, observables=None, order: int = 1):
     """Repeat the step nsteps times.  With a drive, H(t_n) = H0 + f(t_n) H1 with
     f taken from f_table[n] at the left end of step n (Sec. III.A coefficient
     form H0 + f(t) H1; first-order steps use t_n).
 
+    order selects the Kraus scheme of kraus_step.
     Returns (rho, records) where records is a list of (step, [values]).
     """
     rho = np.array(rho0, dtype=np.complex128, copy=True)
@@ -200,7 +223,7 @@ def evolve(rho0, H0: Operator, Ls, h: float, nsteps: int, H1: Operator | None = 
         recs.append((0, [obs(rho) for obs in observables]))
     for n in range(nsteps):
         H = H0 if H1 is None else H0 + H1.scale(float(f_table[n]))
-        rho = kraus_step(rho, H, Ls, h)
+        rho = kraus_step(rho, H, Ls, h, order=order)
         if record_every and observables and ((n + 1) % record_every == 0 or n + 1 == nsteps):
             recs.append((n + 1, [obs(rho) for obs in observables]))
     return rho, recs

@@ -22,11 +22,11 @@ class DenseSystem:
     def rho0(self):
         return D.pure(D.product_vector(self.init))
 
-    def evolve(self, h, nsteps, record_every, names=None):
+    def evolve(self, h, nsteps, record_every, names=None, order=1):
         names = names or list(self.observables)
         obs = [lambda r, O=self.observables[n]: D.expectation(r, O).real for n in names]
         rho, recs = D.evolve(self.rho0(), self.H0, self.Ls, h, nsteps, H1=self.H1, f_table=self.f_table,
-                             record_every=record_every, observables=obs)
+                             record_every=record_every, observables=obs, order=order)
         return rho, recs
 
 

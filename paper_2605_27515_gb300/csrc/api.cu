@@ -562,6 +562,18 @@ QLB_API qlb_status qlb_add_jump(qlb_system* sys, const qlb_op* L) {
   return QLB_OK;
 }
 
+QLB_API qlb_status qlb_set_scheme(qlb_system* sys, int order) {
+  CHECK_ARG(sys, "null argument");
+  CHECK_ARG(order == 1 || order == 2, "scheme order must be 1 or 2");
+  CHECK_ARG(order == 1 || !sys->H1, "the second-order scheme needs a time-independent Hamiltonian");
+  CHECK_ARG(order == 1 || sys->jumps.size() <= 6, "the second-order scheme takes at most 6 jump operators");
+  if (sys->order != order) {
+    sys->order = order;
+    sys->version++;
+  }
+  return QLB_OK;
+}
+
 // ------------------------------------------------------------------ states
 
 QLB_API qlb_status qlb_state_init_product(qlb_system* sys, const double* const* mode_vecs, qlb_state** out) {

@@ -79,6 +79,7 @@ struct qlb_system {
   int64_t n_f = 0;
   std::vector<const qlb_op*> jumps;
   int version = 0;  // bumped when H or jumps change
+  int order = 1;    // Kraus scheme order (1 or 2)
   // Kraus MPO of the last (dt, version) built by any state of this system; new
   // states copy it instead of rebuilding (owned, freed with the system)
   qlb::Kraus* kraus_tmpl = nullptr;

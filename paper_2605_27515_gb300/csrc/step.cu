@@ -339,6 +339,55 @@ static qlb_status kraus_copy(qlb_ctx* ctx, const Kraus& src, Kraus& dst) {
   return QLB_OK;
 }
 
+// Product of two terms of operators, mode by mode: out = scale * op(a) * b with
+// op(a) = a or a^dag.  Dense products are appended to tmp (freed by the caller);
+// factors that need no product are borrowed.  Recipes (keys) compose so that the
+// context's MPO cache recognises repeated products of built-in factors.
+static qlb_status term_mul(qlb_system* sys, const DevTerm& a, bool dag_a, const DevTerm& b, zd scale, DevTerm& out,
+                           std::vector<zd*>& tmp) {
+  qlb_ctx* ctx = sys->ctx;
+  qlb_status s;
+  out.coeff = cmul(cmul(dag_a ? cconj(a.coeff) : a.coeff, b.coeff), scale);
+  out.fac.assign(sys->M, nullptr);
+  out.key.assign(sys->M, "");
+  for (int m = 0; m < sys->M; m++) {
+    int N = 1 << sys->R[m];
+    const zd* A = a.fac[m];
+    const zd* Bm = b.fac[m];
+    if (!A && !Bm) continue;
+    const std::string& ka = a.key[m];
+    const std::string& kb = b.key[m];
+    if (!A)
+      out.key[m] = kb;
+    else if (!Bm)
+      out.key[m] = ka.empty() ? std::string() : (dag_a ? "dag(" + ka + ")" : ka);
+    else if (!ka.empty() && !kb.empty())
+      out.key[m] = (dag_a ? "dag(" + ka + ")" : "(" + ka + ")") + "*(" + kb + ")";
+    if (!A) {
+      out.fac[m] = const_cast<zd*>(Bm);
+      continue;
+    }
+    if (!Bm && !dag_a) {
+      out.fac[m] = const_cast<zd*>(A);
+      continue;
+    }
+    zd* P = nullptr;
+    if (Bm) {
+      if ((s = dense_mul(ctx, A, dag_a ? OP_C : OP_N, Bm, N, &P))) return s;
+    } else {  // A^dag alone
+      zd* I = nullptr;
+      qlb_factor f{m, QLB_F_ID, 1, 0.0, nullptr};
+      if ((s = make_factor(ctx, N, f, &I))) return s;
+      s = dense_mul(ctx, A, OP_C, I, N, &P);
+      dev_free(ctx, I);
+      if (s) return s;
+    }
+    tmp.push_back(P);
+    out.fac[m] = P;
+  }
+  return QLB_OK;
+}
+
 static qlb_status build_kraus_fresh(qlb_state* st, double dt);
 
 qlb_status build_kraus(qlb_state* st, double dt) {
@@ -362,81 +411,109 @@ static qlb_status build_kraus_fresh(qlb_state* st, double dt) {
   qlb_ctx* ctx = sys->ctx;
   kraus_clear(ctx, st->kraus);
   qlb_status s;
-  // U_1 terms
-  std::vector<DevTerm> terms;
-  std::vector<zd*> tmp;
-  DevTerm id;
-  id.coeff = mk<double>(1.0, 0.0);
-  id.fac.assign(sys->M, nullptr);
-  id.key.assign(sys->M, "");
-  terms.push_back(id);
-  if (sys->H0)
-    for (auto& t : sys->H0->terms) {
-      DevTerm u = t;
-      u.coeff = cmul(t.coeff, mk<double>(0.0, -dt));
-      terms.push_back(u);
+  if (sys->order == 2 && (sys->H1 || sys->jumps.size() > 6)) {
+    set_error("the second-order scheme needs H1 == NULL and at most 6 jump operators");
+    return QLB_EINVAL;
+  }
+  // H_eff = H0 - (i/2) sum_k L_k^dag L_k (Sec. V.B), L^dag L formed term by term
+  std::vector<zd*> tmp;  // dense products made for this build
+  struct Tmp {
+    qlb_ctx* c;
+    std::vector<zd*>& v;
+    ~Tmp() {
+      for (auto p : v) dev_free(c, p);
     }
+  } tmp_guard{ctx, tmp};
+  std::vector<DevTerm> heff;
+  if (sys->H0)
+    for (auto& t : sys->H0->terms) heff.push_back(t);
   double gamma_bound = 0.0;
   for (const qlb_op* L : sys->jumps) {
     gamma_bound += L->inf_norm_bound * L->inf_norm_bound;
     for (auto& ta : L->terms)
       for (auto& tb : L->terms) {
         DevTerm u;
-        // (c_a F_a)^dag (c_b F_b) = conj(c_a) c_b F_a^dag F_b, mode by mode
-        u.coeff = cmul(cconj(ta.coeff), tb.coeff);
-        u.coeff = cscale(u.coeff, -0.5 * dt);  // -i h * (-i/2) = -h/2
-        u.fac.assign(sys->M, nullptr);
-        u.key.assign(sys->M, "");
-        for (int m = 0; m < sys->M; m++) {
-          int N = 1 << sys->R[m];
-          const zd* A = ta.fac[m];
-          const zd* B = tb.fac[m];
-          if (!A && !B) continue;
-          const std::string& ka = ta.key[m];
-          const std::string& kb = tb.key[m];
-          if ((!A || !ka.empty()) && (!B || !kb.empty()))
-            u.key[m] = (A ? "dag(" + ka + ")" : std::string()) + (A && B ? "*" : "") + (B ? "(" + kb + ")" : "");
-          zd* P = nullptr;
-          if (A && B)
-            s = dense_mul(ctx, A, OP_C, B, N, &P);
-          else if (A) {  // A^dag
-            zd* I = nullptr;
-            qlb_factor f{m, QLB_F_ID, 1, 0.0, nullptr};
-            if ((s = make_factor(ctx, N, f, &I))) return s;
-            s = dense_mul(ctx, A, OP_C, I, N, &P);
-            dev_free(ctx, I);
-          } else {
-            P = nullptr;
-            s = QLB_OK;
-            u.fac[m] = const_cast<zd*>(B);
-            continue;
-          }
-          if (s) return s;
-          tmp.push_back(P);
-          u.fac[m] = P;
-        }
-        terms.push_back(u);
+        if ((s = term_mul(sys, ta, true, tb, mk<double>(0.0, -0.5), u, tmp))) return s;
+        heff.push_back(u);
       }
   }
-  Mpo U1;
-  s = mpo_from_terms(sys, terms, 1e-30, 0, U1);
-  for (auto p : tmp) dev_free(ctx, p);
-  if (s) return s;
-  // stack U_1 and sqrt(h) L_k
-  std::vector<Mpo> Lk(sys->jumps.size());
-  std::vector<const Mpo*> parts = {&U1};
-  std::vector<int> rows = {0};
-  for (size_t k = 0; k < sys->jumps.size(); k++) {
-    if ((s = mpo_copy(ctx, sys->jumps[k]->mpo, Lk[k]))) return s;
-    if ((s = mpo_scale(ctx, Lk[k], mk<double>(std::sqrt(dt), 0.0)))) return s;
-    parts.push_back(&Lk[k]);
-    rows.push_back((int)k + 1);
+  DevTerm id;
+  id.coeff = mk<double>(1.0, 0.0);
+  id.fac.assign(sys->M, nullptr);
+  id.key.assign(sys->M, "");
+  // U_1 = 1 - i h H_eff
+  std::vector<DevTerm> u1 = {id};
+  for (auto& t : heff) {
+    DevTerm u = t;
+    u.coeff = cmul(t.coeff, mk<double>(0.0, -dt));
+    u1.push_back(u);
   }
-  int B = 1 + (int)sys->jumps.size();
+  // Kraus operators of the scheme, branch k on the left boundary (Sec. V.B):
+  //   order 1: U_1, sqrt(h) L_k
+  //   order 2: U_1' = U_1 - (h^2/2) H_eff^2, sqrt(h/2) U_1 L_k, sqrt(h/2) L_k U_1,
+  //            (h/sqrt 2) L_j L_k   (K = U' + (h/2)(U L + L U) + (h^2/2) L^2)
+  std::vector<std::vector<DevTerm>> branches;
+  const size_t l = sys->jumps.size();
+  if (sys->order == 1) {
+    branches.push_back(u1);  // the jump branches reuse the operators' own MPOs below
+  } else {
+    std::vector<DevTerm> u1p = u1;
+    for (auto& a : heff)
+      for (auto& b : heff) {
+        DevTerm u;
+        if ((s = term_mul(sys, a, false, b, mk<double>(-0.5 * dt * dt, 0.0), u, tmp))) return s;
+        u1p.push_back(u);
+      }
+    branches.push_back(u1p);
+    const double r = std::sqrt(0.5 * dt);
+    for (int side = 0; side < 2; side++)
+      for (size_t k = 0; k < l; k++) {
+        std::vector<DevTerm> b;
+        for (auto& x : u1)
+          for (auto& y : sys->jumps[k]->terms) {
+            DevTerm u;
+            if ((s = side == 0 ? term_mul(sys, x, false, y, mk<double>(r, 0.0), u, tmp)
+                               : term_mul(sys, y, false, x, mk<double>(r, 0.0), u, tmp)))
+              return s;
+            b.push_back(u);
+          }
+        branches.push_back(b);
+      }
+    for (size_t j = 0; j < l; j++)
+      for (size_t k = 0; k < l; k++) {
+        std::vector<DevTerm> b;
+        for (auto& x : sys->jumps[j]->terms)
+          for (auto& y : sys->jumps[k]->terms) {
+            DevTerm u;
+            if ((s = term_mul(sys, x, false, y, mk<double>(dt / std::sqrt(2.0), 0.0), u, tmp))) return s;
+            b.push_back(u);
+          }
+        branches.push_back(b);
+      }
+  }
+  const int B = sys->order == 1 ? (int)(1 + l) : (int)branches.size();
+  std::vector<Mpo> bm(B);
+  struct Parts {
+    qlb_ctx* c;
+    std::vector<Mpo>& v;
+    ~Parts() {
+      for (auto& m : v) mpo_clear(c, m);
+    }
+  } parts_guard{ctx, bm};
+  std::vector<const Mpo*> parts;
+  std::vector<int> rows;
+  for (int k = 0; k < B; k++) {
+    if (k < (int)branches.size()) {
+      if ((s = mpo_from_terms(sys, branches[k], 1e-30, 0, bm[k]))) return s;
+    } else {
+      if ((s = mpo_copy(ctx, sys->jumps[k - 1]->mpo, bm[k]))) return s;
+      if ((s = mpo_scale(ctx, bm[k], mk<double>(std::sqrt(dt), 0.0)))) return s;
+    }
+    parts.push_back(&bm[k]);
+    rows.push_back(k);
+  }
   Mpo S;
   if ((s = mpo_stack(ctx, parts, rows, B, S))) return s;
-  mpo_clear(ctx, U1);
-  for (auto& m : Lk) mpo_clear(ctx, m);
   if ((s = mpo_compress(ctx, S, 1e-30, 0))) return s;
   Kraus& K = st->kraus;
   if (sys->H1) {

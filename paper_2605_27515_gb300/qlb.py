@@ -67,6 +67,7 @@ _SIGS = {
     "qlb_op_to_dense": (_st, [_vp, C.POINTER(C.c_double), C.c_size_t]),
     "qlb_set_hamiltonian": (_st, [_vp, _vp, _vp, C.POINTER(C.c_double), C.c_int64]),
     "qlb_add_jump": (_st, [_vp, _vp]),
+    "qlb_set_scheme": (_st, [_vp, C.c_int]),
     "qlb_state_init_product": (_st, [_vp, C.POINTER(C.POINTER(C.c_double)), C.POINTER(_vp)]),
     "qlb_state_destroy": (None, [_vp]),
     "qlb_truncate": (_st, [_vp, C.c_double, C.c_int, C.c_int]),
@@ -236,6 +237,10 @@ class System:
     def add_jump(self, L):
         _check(self.lib.qlb_add_jump(self.h, L.h))
         self._keep.append(L)
+
+    def set_scheme(self, order: int):
+        """Kraus scheme order of qlb_step: 1 (K = U + hL) or 2 (second-order map)."""
+        _check(self.lib.qlb_set_scheme(self.h, int(order)))
 
     def state(self, mode_vecs) -> "State":
         arrs = [_cvec(v) for v in mode_vecs]

@@ -5,7 +5,8 @@ absolute of the dense FP64 oracle (the truncated-form tolerance).
 
 * large cat mode at its check size N = 128, alpha^2 = 16, Zeno drive, literal
   dt = 5e-4 (recorded before the explicit step's instability takes over, and the
-  stable twin dt = 1e-4 over a longer window);
+  stable twin dt = 1e-4 over a longer window, in both precision forms);
+* the second-order Kraus scheme on the N = 32 cat;
 * transmon x resonator at 32 charge states x 64 Fock levels with the ramped drive;
 * the two coupled cats with buffers at (N_b, N_a, N_a, N_b) = (4, 8, 8, 4).
 """
@@ -21,9 +22,9 @@ from paper_2605_27515_gb300 import systems
 pytestmark = pytest.mark.gpu
 
 
-def _compare(b, ds, dt, nsteps, every, names):
+def _compare(b, ds, dt, nsteps, every, names, order=1):
     st = b.sys.state(b.init)
-    _, recs = ds.evolve(dt, nsteps, every, names=names)
+    _, recs = ds.evolve(dt, nsteps, every, names=names, order=order)
     worst = {n: 0.0 for n in names}
     done = 0
     for step, vals in recs[1:]:
@@ -36,13 +37,26 @@ def _compare(b, ds, dt, nsteps, every, names):
     return worst
 
 
-@pytest.mark.parametrize("dt,nsteps,zipf", [(5e-4, 100, 1e-2), (1e-4, 600, 1e-2), (1e-4, 600, 1e-6)])
-def test_cat_r9_check_size(dt, nsteps, zipf):
+@pytest.mark.parametrize("dt,nsteps,precision", [(5e-4, 100, Q.PREC_F64), (1e-4, 600, Q.PREC_F64),
+                                                  (1e-4, 600, Q.PREC_MIXED)])
+def test_cat_r9_check_size(dt, nsteps, precision):
     cfg = inputs.config("cat_r9")
     cfg.update(cfg.pop("check"))  # N = 128, alpha^2 = 16
-    c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"], zip_tol_factor=zipf)
+    c = Q.Ctx(device=0, precision=precision, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])
     b = systems.build(c, cfg)
     worst = _compare(b, OS.cat(cfg), dt, nsteps, 20, ["n", "parity"])
+    assert max(worst.values()) < 1e-6, worst
+    c.close()
+
+
+def test_cat_r5_second_order():
+    """The second-order scheme on the N = 32 cat (truncated form): within 1e-6 of
+    the dense oracle's second-order map over 1000 steps of dt = 1e-3."""
+    cfg = inputs.config("cat_r5")
+    c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])
+    b = systems.build(c, cfg)
+    b.sys.set_scheme(2)
+    worst = _compare(b, OS.cat(cfg), cfg["dt"], 1000, 100, ["n", "parity"], order=2)
     assert max(worst.values()) < 1e-6, worst
     c.close()
 

@@ -147,6 +147,95 @@ def test_untruncated_step_matches_dense(ctx, Rs):
     s.close()
 
 
+def _second_order_branches(Hd, Lds, h):
+    """The Kraus operators of the second-order map in branch order:
+    U_1', sqrt(h/2) U_1 L_k, sqrt(h/2) L_k U_1, (h/sqrt 2) L_j L_k (Sec. V.B)."""
+    He = D.h_eff(Hd, Lds)
+    U = D.u1(Hd, Lds, h)
+    out = [(U + (He @ He).scale(-0.5 * h * h)).dense()]
+    out += [np.sqrt(h / 2) * (U @ L).dense() for L in Lds]
+    out += [np.sqrt(h / 2) * (L @ U).dense() for L in Lds]
+    out += [h / np.sqrt(2) * (Lj @ Lk).dense() for Lj in Lds for Lk in Lds]
+    return out
+
+
+@pytest.mark.parametrize("Rs", [[3], [2, 2]])
+def test_second_order_kraus_branches(ctx, Rs):
+    """Each branch of the device's stacked second-order Kraus MPO equals the dense
+    product it stands for (1 + 2l + l^2 branches)."""
+    s, H, Ls, Hd, Lds, vecs, _, dims = _random_system(ctx, Rs, seed=41 + len(Rs))
+    s.set_scheme(2)
+    st = s.state(vecs)
+    h = 0.03
+    ref = _second_order_branches(Hd, Lds, h)
+    assert len(ref) == 1 + 2 * len(Lds) + len(Lds) ** 2
+    for k, K in enumerate(ref):
+        np.testing.assert_allclose(st.kraus_to_dense(h, k), K, atol=1e-12 * max(1.0, np.abs(K).max()))
+    st.close()
+    s.close()
+
+
+@pytest.mark.parametrize("Rs", [[3], [2, 2], [1, 2, 1]])
+def test_second_order_step_matches_dense(ctx, Rs):
+    """Untruncated second-order steps: the whole density matrix within 1e-10 of the
+    dense oracle's second-order map, step after step."""
+    s, H, Ls, Hd, Lds, vecs, _, dims = _random_system(ctx, Rs, seed=sum(Rs) * 11 + len(Rs))
+    s.set_scheme(2)
+    st = s.state(vecs)
+    rho = D.pure(D.product_vector([v / np.linalg.norm(v) for v in vecs]))
+    h = 0.02
+    for k in range(8):
+        assert st.step(h, 1) >= 0
+        rho = D.kraus_step(rho, Hd, Lds, h, order=2)
+        Psi = st.to_dense()
+        np.testing.assert_allclose(Psi @ Psi.conj().T, rho, atol=1e-10)
+        assert abs(st.trace() - 1) < 1e-12
+    st.close()
+    s.close()
+
+
+def test_second_order_global_error_against_lindblad(ctx):
+    """Through the device path, halving h divides the error against exp(T Lindbladian)
+    by about 4 with the second-order scheme and about 2 with the first-order one."""
+    import scipy.linalg as sla
+
+    s, H, Ls, Hd, Lds, vecs, _, dims = _random_system(ctx, [3], seed=77)
+    rho0 = D.pure(D.product_vector([v / np.linalg.norm(v) for v in vecs]))
+    T = 0.4
+    G = D.lindbladian(Hd, Lds)
+    exact = (sla.expm(T * G) @ rho0.reshape(-1)).reshape(rho0.shape)
+    exact = exact / np.trace(exact).real
+    errs = {}
+    for order in (1, 2):
+        s.set_scheme(order)
+        for n in (20, 40):
+            st = s.state(vecs)
+            st.step(T / n, n)
+            Psi = st.to_dense()
+            errs[order, n] = np.abs(Psi @ Psi.conj().T - exact).max()
+            st.close()
+    r1 = errs[1, 20] / errs[1, 40]
+    r2 = errs[2, 20] / errs[2, 40]
+    assert 1.6 < r1 < 2.5, errs
+    assert 3.2 < r2 < 5.0, errs
+    assert errs[2, 40] < errs[1, 40] / 5
+    s.close()
+
+
+def test_second_order_scheme_errors(ctx):
+    s = Q.System(ctx, [3])
+    with pytest.raises(Q.QlbError) as e:
+        s.set_scheme(3)
+    assert e.value.status == Q.EINVAL
+    H0 = s.op([(1.0, [(0, Q.F_NUM)])])
+    H1 = s.op([(1.0, [(0, Q.F_A)]), (1.0, [(0, Q.F_ADAG)])])
+    s.set_hamiltonian(H0, H1, np.ones(4))
+    with pytest.raises(Q.QlbError) as e:
+        s.set_scheme(2)
+    assert e.value.status == Q.EINVAL
+    s.close()
+
+
 def test_drive_table_matches_dense(ctx):
     """H(t_n) = H0 + f(t_n) H1 with f taken at the left end of each step."""
     R = 3

@@ -3,6 +3,7 @@ respects the device-memory budget (continuous batching of independent solves).""
 import numpy as np
 import pytest
 
+from oracle import systems as OS
 from paper_2605_27515_gb300 import inputs
 from paper_2605_27515_gb300 import qlb as Q
 from paper_2605_27515_gb300 import serving
@@ -11,9 +12,12 @@ pytestmark = pytest.mark.gpu
 
 
 def _requests(n, seed=5):
+    """The serving mix at test size: Fock sizes up to N = 64 and a step that the
+    explicit scheme keeps stable there (h sum_k ||L_k||^2 < 4)."""
     reqs = inputs.serving_requests(n=n, seed=seed)
     for r in reqs:
-        r["R"] = min(r["R"], 7)  # keep the test quick
+        r["R"] = min(r["R"], 6)
+        r["dt"] = 2e-4
     return reqs
 
 
@@ -46,4 +50,21 @@ def test_admission_respects_budget():
     assert srv.peak_live <= 2
     lat = [j.done - j.arrival for j in jobs]
     assert all(np.isfinite(lat))
+    ctx.close()
+
+
+def test_served_results_match_oracle():
+    """Each served request, run in the mix, within 1e-6 of the dense oracle at its own
+    Fock size (photon number and parity at completion)."""
+    reqs = _requests(3, seed=13)
+    ctx = Q.Ctx(device=0, chi_max=64, chi_mu_max=8, stream_ordered=1)
+    srv = serving.Server(ctx, chunk=50)
+    jobs = srv.run(reqs, step_scale=0.02, time_scale=0.0)
+    for j in jobs:
+        r = j.req
+        cfg = dict(kind="cat", R=[r["R"]], alpha2=r["alpha2"], k2=1.0, k1=r["k1_over_k2"], eps_z=0.0)
+        _, recs = OS.cat(cfg).evolve(r["dt"], j.steps, j.steps, names=["n", "parity"])
+        n_o, p_o = recs[-1][1]
+        assert abs(j.result["n"] - n_o) < 1e-6, (r["id"], j.result, n_o)
+        assert abs(j.result["parity"] - p_o) < 1e-6, (r["id"], j.result, p_o)
     ctx.close()

@@ -100,6 +100,39 @@ def test_first_order_local_error_against_eq1():
     assert 3.5 < e1 / e2 < 4.5
 
 
+def _local_error2(H, Ls, rho, h):
+    G = D.lindbladian(H, Ls)
+    exact = (scipy.linalg.expm(h * G) @ rho.reshape(-1)).reshape(rho.shape)
+    return np.linalg.norm(D.kraus_step(rho, H, Ls, h, normalize=False, order=2) - exact)
+
+
+def test_second_order_local_error_against_eq1():
+    """K = U' + (h/2)(UL + LU) + (h^2/2) L^2 agrees with the flow of Eq. 1 to O(h^3)."""
+    H, Ls, rho = _rand_system((5,), 2, seed=3)
+    e1 = _local_error2(H, Ls, rho, 4e-3)
+    e2 = _local_error2(H, Ls, rho, 2e-3)
+    assert 7.0 < e1 / e2 < 9.0
+    # and it is an order better than the first-order map at the same h
+    assert e2 < 0.05 * _local_error(H, Ls, rho, 2e-3)
+
+
+def test_second_order_superoperator():
+    """Brute force: the second-order map as a matrix on vec(rho), built from the
+    Kraus operators U_1', sqrt(h/2) U_1 L_k, sqrt(h/2) L_k U_1, (h/sqrt 2) L_j L_k."""
+    H, Ls, rho = _rand_system((4, 2), 2, seed=21)
+    h = 0.01
+    U = D.u1(H, Ls, h).dense()
+    He = D.h_eff(H, Ls).dense()
+    Up = U - 0.5 * h * h * He @ He
+    Ld = [L.dense() for L in Ls]
+    ks = [Up] + [np.sqrt(h / 2) * U @ L for L in Ld] + [np.sqrt(h / 2) * L @ U for L in Ld]
+    ks += [h / np.sqrt(2) * A @ B for A in Ld for B in Ld]
+    S = sum(np.kron(K, K.conj()) for K in ks)
+    ref = (S @ rho.reshape(-1)).reshape(rho.shape)
+    ref /= np.trace(ref).real
+    np.testing.assert_allclose(D.kraus_step(rho, H, Ls, h, order=2), ref, atol=1e-13)
+
+
 # ---------------------------------------------------------------- closed forms
 
 
