@@ -8,8 +8,9 @@
 // (Golub & Van Loan, sym.schur2); G <- J^dag G J, V <- V J.  A pair is skipped
 // when |G_pq| <= n eps sqrt(|G_pp G_qq|) (the relative criterion that keeps small
 // eigenvalues of a Gram matrix accurate) or below an absolute floor of
-// 2 eps^2 Tr G; a sweep with no rotation ends the solve.  At the sweep limit the
-// solve is accepted when the off-diagonal norm left is below n eps Tr G.
+// eps Tr G / 10, under the rounding already carried by the Gram matrix itself;
+// a sweep with no rotation ends the solve.  At the sweep limit the solve is
+// accepted when the off-diagonal norm left is below n eps Tr G.
 //
 // Each round has three barriers: rotation parameters, row update (J^dag G), and
 // column update (G J, V J) which also writes the annihilated entries as exact
@@ -19,6 +20,8 @@
 // Instantiated for R = double (the FP64 form) and R = df64, a pair of floats
 // (the mixed form): the same rotations on the FP32 pipes with ~48-bit significands.
 // Input G and the output vectors are FP64 in both cases.
+
+#include <type_traits>
 
 #include "df64.cuh"
 #include "qlb_internal.cuh"
@@ -121,11 +124,14 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
     s_bad = 0;
     double tr = 0;
     for (int i = 0; i < n; i++) tr += fabs(G[(long)i * n + i].re);
-    // absolute floor 2 eps^2 Tr G: couplings below it change no eigenvalue above
-    // eps^2 Tr G.  Noise among the null directions of a rank-deficient Gram matrix
-    // can keep rotating above it; the solve then stops at the sweep limit and is
-    // accepted when the off-diagonal norm left is below n eps Tr G (its rounding).
-    s_thr = to_r<R>(Eps<R>::v * Eps<R>::v * 2.0 * tr);
+    // absolute floor eps Tr G / 10: G = M M^dag formed in floating point already
+    // carries errors of order eps Tr G in every entry, so couplings below a tenth
+    // of that move no eigenvalue or vector beyond what G itself fixes, and
+    // rotating them only chases rounding noise (among the null directions of a
+    // rank-deficient G above all).  Should noise still keep rotating, the solve
+    // stops at the sweep limit and is accepted when the off-diagonal norm left is
+    // below n eps Tr G.
+    s_thr = to_r<R>(0.1 * Eps<R>::v * tr);
     s_tr = tr;
   }
   __syncthreads();
@@ -317,8 +323,14 @@ template <typename R>
 cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof) {
   size_t want = eig_smem_bytes<R>(e.n_max);
   int dyn = (int)(want <= EIG_SMEM_LIMIT ? want : EIG_SMEM_LIMIT);
+  // FP64: the DFMA pipe bounds the rotations, a few warps keep it busy.  Double-
+  // float: long dependent FP32 chains per rotation, so a full CTA of warps hides
+  // their latency.
+  constexpr bool wide = std::is_same<R, df64>::value;
   if (e.n_max <= 24)
     k_eig<R, 128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+  else if (wide)
+    k_eig<R, 1024><<<1, 1024, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
   else if (e.n_max <= 64)
     k_eig<R, 256><<<1, 256, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
   else
@@ -335,6 +347,7 @@ void init_kernel_attributes() {
   set_attr<df64, 128>();
   set_attr<df64, 256>();
   set_attr<df64, 512>();
+  set_attr<df64, 1024>();
 }
 
 }  // namespace qlb

@@ -37,8 +37,8 @@ def _compare(b, ds, dt, nsteps, every, names, order=1):
     return worst
 
 
-@pytest.mark.parametrize("dt,nsteps,precision", [(5e-4, 100, Q.PREC_F64), (1e-4, 600, Q.PREC_F64),
-                                                  (1e-4, 600, Q.PREC_MIXED)])
+@pytest.mark.parametrize("dt,nsteps,precision", [(5e-4, 100, Q.PREC_F64), (1e-4, 400, Q.PREC_F64),
+                                                  (1e-4, 400, Q.PREC_MIXED)])
 def test_cat_r9_check_size(dt, nsteps, precision):
     cfg = inputs.config("cat_r9")
     cfg.update(cfg.pop("check"))  # N = 128, alpha^2 = 16
@@ -51,12 +51,12 @@ def test_cat_r9_check_size(dt, nsteps, precision):
 
 def test_cat_r5_second_order():
     """The second-order scheme on the N = 32 cat (truncated form): within 1e-6 of
-    the dense oracle's second-order map over 1000 steps of dt = 1e-3."""
+    the dense oracle's second-order map over 300 steps of dt = 1e-3."""
     cfg = inputs.config("cat_r5")
     c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])
     b = systems.build(c, cfg)
     b.sys.set_scheme(2)
-    worst = _compare(b, OS.cat(cfg), cfg["dt"], 1000, 100, ["n", "parity"], order=2)
+    worst = _compare(b, OS.cat(cfg), cfg["dt"], 300, 50, ["n", "parity"], order=2)
     assert max(worst.values()) < 1e-6, worst
     c.close()
 
