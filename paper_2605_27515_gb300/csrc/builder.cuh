@@ -19,6 +19,8 @@ template <typename R>
 cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof);
 template <typename R>
 size_t eig_smem_bytes(int n_max);
+// device workspace (complex elements) the eigen-solvers need beyond shared memory
+size_t eig_workspace_elems(int n_max);
 void init_kernel_attributes();
 
 qlb_status svd_osj(qlb_ctx* ctx, zd* X, int m, int n, double tol, int cap, zd** U, int u_scale, zd** Rr,

@@ -94,5 +94,6 @@ __device__ __forceinline__ bool isfinite(df64 a) { return ::isfinite(a.hi); }
 __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
 __device__ __forceinline__ double fabs(double x) { return ::fabs(x); }
 __device__ __forceinline__ bool isfinite(double x) { return ::isfinite(x); }
+__host__ __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
 
 }  // namespace qlb

@@ -85,6 +85,71 @@ __device__ int keep_count_dev(const double* w, int n, double tol, int cap, doubl
   return k < 1 ? 1 : k;
 }
 
+// Shared end of both eigen-solvers: eigenvalues lam[0..n) (unsorted, in shared
+// memory) and eigenvectors V(i, j) = V[i * vr + j * vc] (component i of vector j)
+// become the sorted weights, the kept count k (written to dims), the weight
+// statistics and the kept vectors in the requested layout.
+template <typename R, int NT>
+__device__ void eig_finish(const EigDesc& e, int* d, int n, const double* lam, const cx<R>* V, long vr, long vc,
+                           bool unconverged, int* s_perm, double* s_w, int* s_k, int* s_bad) {
+  const int tid = threadIdx.x;
+  // eigenvalues, sorted descending (stable on index)
+  for (int i = tid; i < n; i += NT) {
+    double li = lam[i];
+    if (!isfinite(li)) *s_bad = 1;
+    int rank = 0;
+    for (int j = 0; j < n; j++) {
+      double lj = lam[j];
+      if (lj > li || (lj == li && j < i)) rank++;
+    }
+    s_perm[rank] = i;
+  }
+  __syncthreads();
+  for (int r = tid; r < n; r += NT) {
+    double l = lam[s_perm[r]];
+    s_w[r] = l > 0.0 ? l : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int cap = dev_eval(e.cap, d);
+    if (cap < 1) cap = 1;
+    int k = *s_bad ? 1 : keep_count_dev(s_w, n, e.tol, cap, e.gap);
+    *s_k = k;
+    d[e.dim_out] = k;
+    double total = 0.0, kept = 0.0;
+    for (int i = 0; i < n; i++) total += s_w[i];
+    for (int i = 0; i < k; i++) kept += s_w[i];
+    if (e.kept_weight) *e.kept_weight = kept;
+    if (e.total_weight) *e.total_weight = total;
+    if (e.disc_stat && total > 0.0) {
+      double r = (total - kept) / total;
+      if (r > *e.disc_stat) *e.disc_stat = r;
+    }
+    if (e.lam)
+      for (int i = 0; i < n; i++) e.lam[i] = s_w[i];
+    if (e.err) {
+      if (unconverged) atomicOr(e.err, 1);
+      if (*s_bad || !isfinite(total)) atomicOr(e.err, 2);
+    }
+  }
+  __syncthreads();
+  const int k = *s_k;
+  zd* out = (zd*)e.out;
+  if (e.out_mode == 0) {
+    for (long x = tid; x < (long)n * k; x += NT) {
+      int i = (int)(x / k), j = (int)(x - (long)i * k);
+      cx<R> v = V[i * vr + s_perm[j] * vc];
+      out[x] = mk<double>(to_d(v.re), to_d(v.im));
+    }
+  } else if (e.out_mode == 1) {
+    for (long x = tid; x < (long)n * k; x += NT) {
+      int j = (int)(x / n), i = (int)(x - (long)j * n);
+      cx<R> v = V[i * vr + s_perm[j] * vc];
+      out[x] = mk<double>(to_d(v.re), -to_d(v.im));
+    }
+  }
+}
+
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R>* work, int dyn_bytes,
                                            double* prof) {
@@ -105,6 +170,7 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
   __shared__ int n_rot;
   __shared__ int s_perm[512];
   __shared__ double s_w[512];
+  __shared__ double s_lam[512];
   __shared__ int s_k;
   __shared__ int s_bad;
   __shared__ R s_thr;
@@ -245,61 +311,273 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
     atomicAdd(prof + QLB_K_COUNT, 2.0 * sizeof(zd) * (double)n * (double)n);
   }
 
-  // eigenvalues, sorted descending (stable on index)
-  for (int i = tid; i < n; i += NT) {
-    double li = to_d(Gs[(long)i * np + i].re);
-    if (!isfinite(li)) s_bad = 1;
-    int rank = 0;
-    for (int j = 0; j < n; j++) {
-      double lj = to_d(Gs[(long)j * np + j].re);
-      if (lj > li || (lj == li && j < i)) rank++;
-    }
-    s_perm[rank] = i;
-  }
+  for (int i = tid; i < n; i += NT) s_lam[i] = to_d(Gs[(long)i * np + i].re);
   __syncthreads();
-  for (int r = tid; r < n; r += NT) {
-    double l = to_d(Gs[(long)s_perm[r] * np + s_perm[r]].re);
-    s_w[r] = l > 0.0 ? l : 0.0;
+  eig_finish<R, NT>(e, d, n, s_lam, Vs, np, 1, unconverged, s_perm, s_w, &s_k, &s_bad);
+}
+
+// One-CTA Hermitian eigen-solve by Householder tridiagonalisation and implicit QL
+// (the FP64 form).  Far fewer flops and barriers than cyclic Jacobi: the DFMA
+// pipe of one SM is the bound, and per solve Jacobi spends ~30 n^3 flops and
+// 3 barriers per round over ~10 sweeps of n - 1 rounds, this solver ~15 n^3 flops
+// and 3 barriers per column plus one per QL step.
+//
+// 1. Tridiagonalisation (Golub & Van Loan, Alg. 8.3.1, complex form).  For column
+//    k the reflector H = I - tau v v^dag with v = x + e^{i phi} |x| e_1,
+//    e^{i phi} = x_1 / |x_1|, tau = 1 / (|x| (|x| + |x_1|)) maps x = A[k+1:, k] to
+//    -e^{i phi} |x| e_1.  The trailing block takes A <- H A H as
+//    A - v w^dag - w v^dag with p = tau A v, w = p - (tau/2)(v^dag p) v, and
+//    Q <- Q H accumulates Q (G = Q T Q^dag).
+// 2. A diagonal phase matrix D turns the complex subdiagonal beta_k into |beta_k|:
+//    d_0 = 1, d_{k+1} = d_k beta_k / |beta_k|; T' = D^dag T D is real symmetric.
+// 3. Implicit QL with the Wilkinson-type shift from the leading 2x2 of the
+//    unreduced block (Bowdler, Martin, Reinsch & Wilkinson, "The QR and QL
+//    algorithms for symmetric matrices", 1968), rotations applied to the columns
+//    of W = Q D, which ends as the eigenvectors of G.  Off-diagonals deflate below
+//    eps (|d_m| + |d_m+1|) or below eps Tr G / 1000.
+//
+// Lane 0 of warp 0 runs the scalar QL recurrence; the other warps apply the
+// rotations of the previous QL step to the rows of W meanwhile (double-buffered
+// rotation lists, one barrier per QL step).  Q and W are stored transposed
+// (Wt[j][i] = W[i][j]) so that a thread per row i reads consecutive words.
+constexpr int HEEV_MAX_IT = 60;
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd* work, int dyn_bytes, double* prof) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = dev_eval(e.n, d);
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  if (n <= 0) {
+    if (tid == 0) d[e.dim_out] = 0;
+    return;
   }
-  __syncthreads();
+  const int np = n + (n & 1);
+  const bool use_smem = 2L * np * np * (long)sizeof(zd) <= (long)dyn_bytes;
+  zd* A = use_smem ? (zd*)smem_raw : work;
+  zd* Qt = A + (long)np * np;
+  __shared__ zd s_v[512], s_p[512], s_u[512];
+  __shared__ double s_d[512], s_e[512];
+  __shared__ double s_rc[2][512], s_rs[2][512];
+  __shared__ int s_rm[2], s_rn[2];
+  __shared__ int s_done[2], s_fail;
+  // per-pass flags are double-buffered: a thread still reading the flag of pass t
+  // after the barrier must not see pass t+1's value
+  __shared__ double s_tau[2], s_tr;
+  __shared__ int s_skip[2];
+  __shared__ int s_perm[512];
+  __shared__ double s_w[512];
+  __shared__ int s_k, s_bad;
+  const double eps = 2.220446049250313e-16;
+
+  const zd* G = (const zd*)e.G;
+  for (long x = tid; x < (long)n * n; x += NT) {
+    int i = (int)(x / n), j = (int)(x - (long)i * n);
+    zd v = G[x];
+    if (i == j) v.im = 0.0;
+    A[(long)i * np + j] = v;
+    Qt[(long)i * np + j] = mk<double>(i == j ? 1.0 : 0.0, 0.0);
+  }
   if (tid == 0) {
-    int cap = dev_eval(e.cap, d);
-    if (cap < 1) cap = 1;
-    int k = s_bad ? 1 : keep_count_dev(s_w, n, e.tol, cap, e.gap);
-    s_k = k;
-    d[e.dim_out] = k;
-    double total = 0.0, kept = 0.0;
-    for (int i = 0; i < n; i++) total += s_w[i];
-    for (int i = 0; i < k; i++) kept += s_w[i];
-    if (e.kept_weight) *e.kept_weight = kept;
-    if (e.total_weight) *e.total_weight = total;
-    if (e.disc_stat && total > 0.0) {
-      double r = (total - kept) / total;
-      if (r > *e.disc_stat) *e.disc_stat = r;
-    }
-    if (e.lam)
-      for (int i = 0; i < n; i++) e.lam[i] = s_w[i];
-    if (e.err) {
-      if (unconverged) atomicOr(e.err, 1);
-      if (s_bad || !isfinite(total)) atomicOr(e.err, 2);
-    }
+    s_bad = 0;
+    s_fail = 0;
+    double tr = 0.0;
+    for (int i = 0; i < n; i++) tr += fabs(G[(long)i * n + i].re);
+    s_tr = tr;
   }
   __syncthreads();
-  const int k = s_k;
-  zd* out = (zd*)e.out;
-  if (e.out_mode == 0) {
-    for (long x = tid; x < (long)n * k; x += NT) {
-      int i = (int)(x / k), j = (int)(x - (long)i * k);
-      cx<R> v = Vs[(long)i * np + s_perm[j]];
-      out[x] = mk<double>(to_d(v.re), to_d(v.im));
+
+  // 1. tridiagonalisation, column by column
+  double flops = 0.0;
+  for (int k = 0; k + 2 < n; k++) {
+    const int m = n - k - 1;  // trailing size
+    const zd* rowk = A + (long)k * np + (k + 1);  // A[k][k+1..] = conj(x)
+    if (tid < 32) {
+      double s2 = 0.0;
+      for (int i = lane; i < m; i += 32) s2 += cabs2(rowk[i]);
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      zd x0 = cconj(rowk[0]);
+      double a0 = sqrt(cabs2(x0));
+      double sig = sqrt(s2);
+      zd ph = a0 > 0.0 ? cscale(x0, 1.0 / a0) : mk<double>(1.0, 0.0);
+      if (s2 > 0.0) {
+        for (int i = lane; i < m; i += 32) s_v[i] = i == 0 ? cscale(ph, a0 + sig) : cconj(rowk[i]);
+      }
+      __syncwarp();  // every lane has read row k before lane 0 overwrites A[k][k+1]
+      if (lane == 0) {
+        s_skip[k & 1] = !(s2 > 0.0);
+        s_tau[k & 1] = s2 > 0.0 ? 1.0 / (sig * (sig + a0)) : 0.0;
+        if (s2 > 0.0) {
+          zd beta = cscale(ph, -sig);
+          A[(long)(k + 1) * np + k] = beta;
+          A[(long)k * np + (k + 1)] = cconj(beta);
+        }
+      }
     }
-  } else if (e.out_mode == 1) {
-    for (long x = tid; x < (long)n * k; x += NT) {
+    __syncthreads();
+    if (s_skip[k & 1]) continue;
+    const double tau = s_tau[k & 1];
+    const long o = (long)(k + 1) * np + (k + 1);  // trailing block origin
+    // p = tau A v (A Hermitian: row i of A is the conjugate of column i) and u = Q v
+    for (int i = tid; i < m; i += NT) {
+      zd acc = mk<double>(0.0, 0.0);
+      for (int j = 0; j < m; j++) cfma(acc, cconj(A[o + (long)j * np + i]), s_v[j]);
+      s_p[i] = cscale(acc, tau);
+    }
+    for (int i = tid; i < n; i += NT) {
+      zd acc = mk<double>(0.0, 0.0);
+      for (int j = 0; j < m; j++) cfma(acc, Qt[(long)(k + 1 + j) * np + i], s_v[j]);
+      s_u[i] = acc;
+    }
+    __syncthreads();
+    // K = (tau/2) v^dag p, computed by every warp
+    double kk = 0.0;
+    for (int i = lane; i < m; i += 32) {
+      zd a = s_v[i], b = s_p[i];
+      kk += a.re * b.re + a.im * b.im;
+    }
+    for (int q = 16; q > 0; q >>= 1) kk += __shfl_xor_sync(0xffffffffu, kk, q);
+    const double K = 0.5 * tau * kk;
+    // A_trailing -= v w^dag + w v^dag,  Q[:, k+1:] -= tau u v^dag
+    for (long x = tid; x < (long)m * m; x += NT) {
+      int i = (int)(x / m), j = (int)(x - (long)i * m);
+      zd vi = s_v[i], vj = s_v[j];
+      zd wi = csub(s_p[i], cscale(vi, K)), wj = csub(s_p[j], cscale(vj, K));
+      zd a = A[o + (long)i * np + j];
+      a = csub(a, cmul(vi, cconj(wj)));
+      a = csub(a, cmul(wi, cconj(vj)));
+      A[o + (long)i * np + j] = a;
+    }
+    for (long x = tid; x < (long)m * n; x += NT) {
       int j = (int)(x / n), i = (int)(x - (long)j * n);
-      cx<R> v = Vs[(long)i * np + s_perm[j]];
-      out[x] = mk<double>(to_d(v.re), -to_d(v.im));
+      long a = (long)(k + 1 + j) * np + i;
+      Qt[a] = csub(Qt[a], cscale(cmul(s_u[i], cconj(s_v[j])), tau));
     }
+    flops += 24.0 * m * m + 16.0 * (double)n * m;
+    __syncthreads();
   }
+
+  // 2. real tridiagonal T' = D^dag T D and W = Q D (rows of Qt scaled)
+  if (tid == 0) {
+    zd ph = mk<double>(1.0, 0.0);
+    for (int k = 0; k < n; k++) {
+      s_d[k] = A[(long)k * np + k].re;
+      s_u[k] = ph;
+      if (k + 1 < n) {
+        zd b = cconj(A[(long)k * np + (k + 1)]);  // subdiagonal, read from the row kept exact
+        double ab = sqrt(cabs2(b));
+        s_e[k] = ab;
+        if (ab > 0.0) ph = cmul(ph, cscale(b, 1.0 / ab));
+      } else {
+        s_e[k] = 0.0;
+      }
+    }
+    s_done[0] = s_done[1] = 0;
+    s_rn[0] = s_rn[1] = 0;
+  }
+  __syncthreads();
+  for (long x = tid; x < (long)n * n; x += NT) {
+    int j = (int)(x / n), i = (int)(x - (long)j * n);
+    long a = (long)j * np + i;
+    Qt[a] = cmul(Qt[a], s_u[j]);
+  }
+  __syncthreads();
+
+  // 3. implicit QL; lane 0 of warp 0 produces the rotations of one QL step per
+  // pass, the other warps apply those of the previous pass to the rows of W.
+  zd* Wt = Qt;
+  const double floor_abs = 1e-3 * eps * s_tr;
+  int ql_l = 0, ql_it = 0;
+  long n_rot = 0;
+  for (int t = 0;; t++) {
+    const int b = t & 1;
+    if (tid == 0) {
+      int cnt = 0, mtop = 0;
+      while (ql_l < n) {
+        int m = ql_l;
+        while (m < n - 1) {
+          double dd = fabs(s_d[m]) + fabs(s_d[m + 1]);
+          double em = fabs(s_e[m]);
+          if (em <= eps * dd || em <= floor_abs) break;
+          m++;
+        }
+        if (m == ql_l) {
+          ql_l++;
+          ql_it = 0;
+          continue;
+        }
+        if (++ql_it > HEEV_MAX_IT) {
+          s_fail = 1;
+          s_e[m - 1] = 0.0;  // give up on this coupling; flagged as unconverged
+          continue;
+        }
+        const int l = ql_l;
+        double g = (s_d[l + 1] - s_d[l]) / (2.0 * s_e[l]);
+        double r = hypot(g, 1.0);
+        g = s_d[m] - s_d[l] + s_e[l] / (g + (g >= 0.0 ? r : -r));
+        double sn = 1.0, cs = 1.0, p = 0.0;
+        bool under = false;
+        mtop = m;
+        for (int i = m - 1; i >= l; i--) {
+          double f = sn * s_e[i], bb = cs * s_e[i];
+          r = hypot(f, g);
+          s_e[i + 1] = r;
+          if (r == 0.0) {
+            s_d[i + 1] -= p;
+            s_e[m] = 0.0;
+            under = true;
+            break;
+          }
+          sn = f / r;
+          cs = g / r;
+          g = s_d[i + 1] - p;
+          r = (s_d[i] - g) * sn + 2.0 * cs * bb;
+          p = sn * r;
+          s_d[i + 1] = g + p;
+          g = cs * r - bb;
+          s_rc[b][cnt] = cs;
+          s_rs[b][cnt] = sn;
+          cnt++;
+        }
+        if (!under) {
+          s_d[l] -= p;
+          s_e[l] = g;
+          s_e[m] = 0.0;
+        }
+        break;  // one QL step per pass
+      }
+      s_rm[b] = mtop;
+      s_rn[b] = cnt;
+      n_rot += cnt;
+      s_done[b] = ql_l >= n;
+    } else if (tid >= 32 && t > 0) {
+      // rotations (i, i+1) for i = m-1, m-2, ... of the previous pass: keep the
+      // running entry of column i+1 in registers
+      const int pb = b ^ 1;
+      const int cnt = s_rn[pb];
+      if (cnt > 0) {
+        const int m = s_rm[pb];
+        for (int row = tid - 32; row < n; row += NT - 32) {
+          zd cur = Wt[(long)m * np + row];
+          for (int j = 0; j < cnt; j++) {
+            const int i = m - 1 - j;
+            const double cs = s_rc[pb][j], sn = s_rs[pb][j];
+            zd a = Wt[(long)i * np + row];
+            Wt[(long)(i + 1) * np + row] = mk<double>(sn * a.re + cs * cur.re, sn * a.im + cs * cur.im);
+            cur = mk<double>(cs * a.re - sn * cur.re, cs * a.im - sn * cur.im);
+          }
+          Wt[(long)(m - cnt) * np + row] = cur;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_done[b]) break;  // a finishing pass produces no rotations
+  }
+  if (prof && tid == 0) {
+    atomicAdd(prof, flops + 8.0 * (double)n * (double)n_rot);
+    atomicAdd(prof + QLB_K_COUNT, 2.0 * sizeof(zd) * (double)n * (double)n);
+  }
+  eig_finish<double, NT>(e, d, n, s_d, Wt, 1, np, s_fail != 0, s_perm, s_w, &s_k, &s_bad);
 }
 
 constexpr size_t EIG_SMEM_LIMIT = 200 * 1024;
@@ -319,8 +597,28 @@ size_t eig_smem_bytes(int n_max) {
 template size_t eig_smem_bytes<double>(int);
 template size_t eig_smem_bytes<df64>(int);
 
+// Dynamic shared memory of the QL solver: its static arrays take ~55 KB of the
+// 227 KB a CTA may hold, so A and W stay in shared memory up to n ~ 70.
+constexpr size_t HEEV_SMEM_LIMIT = 160 * 1024;
+
+size_t eig_workspace_elems(int n_max) {
+  int np = n_max + (n_max & 1);
+  size_t need = 2 * (size_t)np * np;
+  return need * sizeof(zd) > HEEV_SMEM_LIMIT ? need : 1;
+}
+
 template <typename R>
 cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof) {
+  if (std::is_same<R, double>::value) {
+    // FP64 form: Householder tridiagonalisation + implicit QL
+    size_t want = eig_smem_bytes<double>(e.n_max);
+    int dyn = want <= HEEV_SMEM_LIMIT ? (int)want : 0;
+    if (e.n_max <= 64)
+      k_heev<128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
+    else
+      k_heev<256><<<1, 256, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
+    return cudaGetLastError();
+  }
   size_t want = eig_smem_bytes<R>(e.n_max);
   int dyn = (int)(want <= EIG_SMEM_LIMIT ? want : EIG_SMEM_LIMIT);
   // FP64: the DFMA pipe bounds the rotations, a few warps keep it busy.  Double-
@@ -348,6 +646,8 @@ void init_kernel_attributes() {
   set_attr<df64, 256>();
   set_attr<df64, 512>();
   set_attr<df64, 1024>();
+  cudaFuncSetAttribute(k_heev<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HEEV_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_heev<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HEEV_SMEM_LIMIT);
 }
 
 }  // namespace qlb

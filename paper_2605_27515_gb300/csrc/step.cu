@@ -641,8 +641,7 @@ qlb_status plan_buffers(qlb_state* st, const Kraus& K) {
   if ((s = realloc_buf(ctx, &st->T2, &t2, nT))) return s;
   if ((s = realloc_buf(ctx, &st->T3, &t3, nT))) return s;
   st->nT = std::max(st->nT, nT);
-  int np = n_eig + (n_eig & 1);
-  size_t new_ew = (eig_smem_bytes<double>(n_eig) > 200 * 1024) ? (size_t)2 * np * np : 1;
+  size_t new_ew = eig_workspace_elems(n_eig);
   if ((s = realloc_buf(ctx, &st->eigw, &st->nEw, new_ew))) return s;
   if (!st->d_lam) {
     if ((s = dev_alloc(ctx, (void**)&st->d_lam, sizeof(double) * 1024))) return s;
