@@ -611,8 +611,9 @@ template <typename R>
 cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof) {
   if (std::is_same<R, double>::value) {
     // FP64 form: Householder tridiagonalisation + implicit QL
+    // the kernel keeps A and W in shared memory whenever the runtime size fits
     size_t want = eig_smem_bytes<double>(e.n_max);
-    int dyn = want <= HEEV_SMEM_LIMIT ? (int)want : 0;
+    int dyn = (int)(want <= HEEV_SMEM_LIMIT ? want : HEEV_SMEM_LIMIT);
     if (e.n_max <= 64)
       k_heev<128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
     else
