@@ -317,10 +317,12 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
 }
 
 // One-CTA Hermitian eigen-solve by Householder tridiagonalisation and implicit QL
-// (the FP64 form).  Far fewer flops and barriers than cyclic Jacobi: the DFMA
-// pipe of one SM is the bound, and per solve Jacobi spends ~30 n^3 flops and
-// 3 barriers per round over ~10 sweeps of n - 1 rounds, this solver ~15 n^3 flops
-// and 3 barriers per column plus one per QL step.
+// (the FP64 form at sizes whose matrices fit in shared memory).  Cyclic Jacobi
+// spends ~30 n^3 flops and 3 barriers per round over ~10 sweeps of n - 1 rounds;
+// this solver ~15 n^3 flops, 3 barriers per column and one per QL step, but the
+// QL bulge chase is a serial chain of ~n^2 dependent rotations, so it wins only
+// while n is small (measured on GB300: 20-200 us at n <= 64, where Jacobi takes
+// several times longer; at n ~ 128 the chain makes it slower than Jacobi).
 //
 // 1. Tridiagonalisation (Golub & Van Loan, Alg. 8.3.1, complex form).  For column
 //    k the reflector H = I - tau v v^dag with v = x + e^{i phi} |x| e_1,
@@ -600,24 +602,25 @@ template size_t eig_smem_bytes<df64>(int);
 // Dynamic shared memory of the QL solver: its static arrays take ~55 KB of the
 // 227 KB a CTA may hold, so A and W stay in shared memory up to n ~ 70.
 constexpr size_t HEEV_SMEM_LIMIT = 160 * 1024;
+constexpr int HEEV_N_MAX = 64;
 
 size_t eig_workspace_elems(int n_max) {
   int np = n_max + (n_max & 1);
   size_t need = 2 * (size_t)np * np;
-  return need * sizeof(zd) > HEEV_SMEM_LIMIT ? need : 1;
+  size_t limit = n_max <= HEEV_N_MAX ? HEEV_SMEM_LIMIT : EIG_SMEM_LIMIT;
+  return need * sizeof(zd) > limit ? need : 1;
 }
 
 template <typename R>
 cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof) {
-  if (std::is_same<R, double>::value) {
-    // FP64 form: Householder tridiagonalisation + implicit QL
-    // the kernel keeps A and W in shared memory whenever the runtime size fits
+  if (std::is_same<R, double>::value && e.n_max <= HEEV_N_MAX) {
+    // FP64 form, shared-memory sizes: Householder tridiagonalisation + implicit QL.
+    // Past HEEV_N_MAX its matrices spill to global memory and the serial QL chain
+    // (~n^2 dependent rotations) outlasts the parallel rounds of Jacobi, which
+    // takes those solves.
     size_t want = eig_smem_bytes<double>(e.n_max);
     int dyn = (int)(want <= HEEV_SMEM_LIMIT ? want : HEEV_SMEM_LIMIT);
-    if (e.n_max <= 64)
-      k_heev<128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
-    else
-      k_heev<256><<<1, 256, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
+    k_heev<128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
     return cudaGetLastError();
   }
   size_t want = eig_smem_bytes<R>(e.n_max);
@@ -648,7 +651,6 @@ void init_kernel_attributes() {
   set_attr<df64, 512>();
   set_attr<df64, 1024>();
   cudaFuncSetAttribute(k_heev<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HEEV_SMEM_LIMIT);
-  cudaFuncSetAttribute(k_heev<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HEEV_SMEM_LIMIT);
 }
 
 }  // namespace qlb
