@@ -850,7 +850,7 @@ static qlb_status prof_collect(qlb_ctx* ctx) {
     float ms = 0;
     QLB_CUDA_TRY(cudaEventElapsedTime(&ms, e.a, e.b));
     ctx->prof_ms[e.kclass] += ms;
-    ctx->prof_launch[e.kclass] += e.kernels;
+    ctx->prof_launch[e.kclass] += 1;
   }
   ctx->prof_events.clear();
   ctx->ev_used = 0;

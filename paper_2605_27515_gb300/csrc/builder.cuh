@@ -21,8 +21,6 @@ template <typename R>
 size_t eig_smem_bytes(int n_max);
 // device workspace (complex elements) the eigen-solvers need beyond shared memory
 size_t eig_workspace_elems(int n_max);
-// kernels one launch_eig call enqueues (the FP64 form may enqueue two, see launch_eig)
-int eig_kernel_count(int n_max, bool mixed);
 void init_kernel_attributes();
 
 qlb_status svd_osj(qlb_ctx* ctx, zd* X, int m, int n, double tol, int cap, zd** U, int u_scale, zd** Rr,

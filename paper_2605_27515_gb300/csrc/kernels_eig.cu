@@ -152,11 +152,10 @@ __device__ void eig_finish(const EigDesc& e, int* d, int n, const double* lam, c
 
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R>* work, int dyn_bytes,
-                                           double* prof, int split) {
+                                           double* prof) {
   extern __shared__ unsigned char smem_raw[];
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
-  if (n <= split) return;  // a solve of this size is taken by the QL kernel
   if (n <= 0) {
     if (tid == 0) d[e.dim_out] = 0;
     return;
@@ -347,13 +346,11 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
 constexpr int HEEV_MAX_IT = 60;
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd* work, int dyn_bytes, double* prof,
-                                            int split) {
+__global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd* work, int dyn_bytes, double* prof) {
   extern __shared__ unsigned char smem_raw[];
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  if (n > split) return;  // a solve of this size is taken by the Jacobi kernel
   if (n <= 0) {
     if (tid == 0) d[e.dim_out] = 0;
     return;
@@ -608,29 +605,24 @@ template size_t eig_smem_bytes<df64>(int);
 constexpr size_t HEEV_SMEM_LIMIT = 160 * 1024;
 constexpr int HEEV_N_MAX = 64;
 
-int eig_kernel_count(int n_max, bool mixed) { return !mixed && n_max > HEEV_N_MAX ? 2 : 1; }
-
 size_t eig_workspace_elems(int n_max) {
   int np = n_max + (n_max & 1);
   size_t need = 2 * (size_t)np * np;
-  // the QL kernel runs only in shared memory; Jacobi spills past EIG_SMEM_LIMIT
-  return n_max > HEEV_N_MAX && need * sizeof(zd) > EIG_SMEM_LIMIT ? need : 1;
+  size_t limit = n_max <= HEEV_N_MAX ? HEEV_SMEM_LIMIT : EIG_SMEM_LIMIT;
+  return need * sizeof(zd) > limit ? need : 1;
 }
 
 template <typename R>
 cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof) {
-  // FP64 form: sizes up to HEEV_N_MAX (known only on the device, from the dims)
-  // go to Householder tridiagonalisation + implicit QL in shared memory.  Past
-  // that its matrices spill to global memory and the serial QL chain (~n^2
-  // dependent rotations) outlasts the parallel rounds of Jacobi, so when the
-  // planned maximum exceeds HEEV_N_MAX both kernels are launched and each returns
-  // at once on the sizes the other takes.
-  int split = -1;
-  if (std::is_same<R, double>::value) {
-    size_t want = eig_smem_bytes<double>(e.n_max < HEEV_N_MAX ? e.n_max : HEEV_N_MAX);
-    k_heev<128><<<1, 128, (int)want, s>>>(e, (int*)d_dims, (zd*)work, (int)want, prof, HEEV_N_MAX);
-    if (e.n_max <= HEEV_N_MAX) return cudaGetLastError();
-    split = HEEV_N_MAX;
+  if (std::is_same<R, double>::value && e.n_max <= HEEV_N_MAX) {
+    // FP64 form, shared-memory sizes: Householder tridiagonalisation + implicit QL.
+    // Past HEEV_N_MAX its matrices spill to global memory and the serial QL chain
+    // (~n^2 dependent rotations) outlasts the parallel rounds of Jacobi, which
+    // takes those solves.
+    size_t want = eig_smem_bytes<double>(e.n_max);
+    int dyn = (int)(want <= HEEV_SMEM_LIMIT ? want : HEEV_SMEM_LIMIT);
+    k_heev<128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
+    return cudaGetLastError();
   }
   size_t want = eig_smem_bytes<R>(e.n_max);
   int dyn = (int)(want <= EIG_SMEM_LIMIT ? want : EIG_SMEM_LIMIT);
@@ -639,13 +631,13 @@ cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void
   // their latency.
   constexpr bool wide = std::is_same<R, df64>::value;
   if (e.n_max <= 24)
-    k_eig<R, 128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, split);
+    k_eig<R, 128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
   else if (wide)
-    k_eig<R, 1024><<<1, 1024, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, split);
+    k_eig<R, 1024><<<1, 1024, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
   else if (e.n_max <= 64)
-    k_eig<R, 256><<<1, 256, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, split);
+    k_eig<R, 256><<<1, 256, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
   else
-    k_eig<R, 512><<<1, 512, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, split);
+    k_eig<R, 512><<<1, 512, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
   return cudaGetLastError();
 }
 template cudaError_t launch_eig<double>(const EigDesc&, const int*, cudaStream_t, void*, double*);

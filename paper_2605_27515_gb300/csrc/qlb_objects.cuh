@@ -55,7 +55,6 @@ struct qlb_ctx {
   struct PEv {
     int kclass;
     cudaEvent_t a, b;
-    int kernels;  // kernels launched between a and b
   };
   std::vector<PEv> prof_events;
   std::vector<cudaEvent_t> ev_pool;

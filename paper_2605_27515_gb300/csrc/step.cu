@@ -160,11 +160,11 @@ static void prof_before(qlb_ctx* ctx, cudaStream_t sm, int kclass, cudaEvent_t* 
   cudaEventRecord(*a, sm);
   (void)kclass;
 }
-static void prof_after(qlb_ctx* ctx, cudaStream_t sm, int kclass, cudaEvent_t a, int kernels = 1) {
+static void prof_after(qlb_ctx* ctx, cudaStream_t sm, int kclass, cudaEvent_t a) {
   if (!ctx->prof_on || !a) return;
   cudaEvent_t b = ctx->ev_pool[ctx->ev_used++];
   cudaEventRecord(b, sm);
-  ctx->prof_events.push_back({kclass, a, b, kernels});
+  ctx->prof_events.push_back({kclass, a, b});
 }
 
 // Opt-in trace for debugging (QLB_DEBUG_DUMP=<file>): after every launch of an
@@ -222,7 +222,7 @@ static qlb_status eig(qlb_state* st, EigDesc& e) {
   // the mixed form runs the same Jacobi in double-float on the FP32 pipes
   cudaError_t r = st->prec == QLB_PREC_MIXED ? launch_eig<df64>(e, st->d_dims, st->stream, st->eigw, pf)
                                              : launch_eig<double>(e, st->d_dims, st->stream, st->eigw, pf);
-  prof_after(ctx, st->stream, QLB_K_EIG, a, eig_kernel_count(e.n_max, st->prec == QLB_PREC_MIXED));
+  prof_after(ctx, st->stream, QLB_K_EIG, a);
   if (r != cudaSuccess) {
     set_error(std::string("eig launch: ") + cudaGetErrorString(r));
     return QLB_EDEVICE;
