@@ -320,10 +320,10 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
 // (the FP64 form at sizes whose matrices fit in shared memory).  Cyclic Jacobi
 // spends ~30 n^3 flops and 3 barriers per round over ~10 sweeps of n - 1 rounds;
 // this solver ~15 n^3 flops, 3 barriers per column and one per QL step, but the
-// QL bulge chase is a serial chain of ~n^2 dependent rotations, so it pays only
-// while n is small (measured on GB300: 20-200 us per solve at n <= 64, while at
-// n ~ 128, with its matrices in global memory, the chain made it slower than
-// Jacobi).
+// QL bulge chase is a serial chain of ~n^2 dependent rotations, so it is used
+// only for small planned sizes (measured on GB300: 20-200 us per solve at
+// n <= 64; at n ~ 128, with its matrices in global memory, the chain made it
+// slower than Jacobi).
 //
 // 1. Tridiagonalisation (Golub & Van Loan, Alg. 8.3.1, complex form).  For column
 //    k the reflector H = I - tau v v^dag with v = x + e^{i phi} |x| e_1,
