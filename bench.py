@@ -214,17 +214,18 @@ def run_gpu(args):
     # end to end through the public API: host mode vector in (init), K steps each
     # followed by a read-back of the photon number; the system's operators and
     # Kraus MPO were built before (setup), as a caller stepping many states would
+    # (the same step indices as the device-timed run: W + K steps from the start)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     st2 = b.sys.state(b.init)
-    for _ in range(args.steps):
+    for _ in range(args.warmup + args.steps):
         st2.step(dt, 1)
         n_obs = st2.expectation(b.observables["n"])
     p_obs = st2.expectation(b.observables["parity"])
     e2e_s = time.perf_counter() - t0
-    e2e_steps = args.steps
+    e2e_steps = args.warmup + args.steps
     h2d = 16 * 512
-    d2h = 16 * (args.steps + 1)
+    d2h = 16 * (e2e_steps + 1)
     st2.close()
 
     line = {
