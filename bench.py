@@ -91,6 +91,23 @@ def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_throughput(local_ms: float, steps: int, device=None):
+    """Whole-job steps/s of independent replicas: every rank ran `steps` steps in
+    `local_ms`; the job lasts as long as its slowest rank (max over ranks).
+    Returns (steps/s over all ranks, the max time in ms)."""
+    import torch
+    import torch.distributed as dist
+
+    world = 1
+    total_ms = local_ms
+    if dist.is_available() and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * steps / (total_ms / 1e3), total_ms
+
+
 def run_reference(args):
     """FP64 dense oracle of the same workload on the host cores (bounded sample)."""
     rank, world, _ = dist_info()
@@ -183,14 +200,11 @@ def run_gpu(args):
                 evs[k][1].record(stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-    ms = [a.elapsed_time(bb) for a, bb in evs]
-    total_ms = float(sum(ms))
     if world > 1:
-        t = torch.tensor([total_ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        dist.barrier()
+    ms = [a.elapsed_time(bb) for a, bb in evs]
+    value, total_ms = replica_throughput(float(sum(ms)), args.steps, device=f"cuda:{dev}")
     bonds_after = st.bond_dims()
-    value = world * args.steps / (total_ms / 1e3)
 
     # kernel-class breakdown of the same steps (events around every launch)
     ctx.profile_enable(True)

@@ -51,23 +51,30 @@ class Job:
     result: dict = field(default_factory=dict)
 
 
+def build_request(ctx: Q.Ctx, r: dict):
+    """System and state of one request: a single cat mode with its own alpha^2, Fock
+    size, loss ratio and bond caps."""
+    cfg = dict(kind="cat", R=[r["R"]], alpha2=r["alpha2"], k2=1.0, k1=r["k1_over_k2"], eps_z=0.0,
+               dt=r["dt"], tol=r["tol"])
+    b = systems.build_cat(ctx, cfg)
+    st = b.sys.state(b.init)
+    st.truncate(chi_max=r["chi_max"], chi_mu_max=r["chi_mu_max"])
+    return b, st
+
+
 class Server:
-    def __init__(self, ctx: Q.Ctx, hbm_budget: int = 2 << 30, max_slots: int = 64, chunk: int = 100):
+    def __init__(self, ctx: Q.Ctx, hbm_budget: int = 2 << 30, max_slots: int = 64, chunk: int = 100,
+                 build=build_request):
         self.ctx = ctx
         self.budget = hbm_budget
         self.max_slots = max_slots
         self.chunk = chunk
+        self.build = build
         self.peak_live = 0
         self.peak_bytes = 0
 
     def _start(self, job: Job):
-        r = job.req
-        cfg = dict(kind="cat", R=[r["R"]], alpha2=r["alpha2"], k2=1.0, k1=r["k1_over_k2"], eps_z=0.0,
-                   dt=r["dt"], tol=r["tol"])
-        b = systems.build_cat(self.ctx, cfg)
-        st = b.sys.state(b.init)
-        st.truncate(chi_max=r["chi_max"], chi_mu_max=r["chi_mu_max"])
-        job.sysb, job.state = b, st
+        job.sysb, job.state = self.build(self.ctx, job.req)
         job.remaining = job.steps
 
     def _finish(self, job: Job, now: float):
