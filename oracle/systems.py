@@ -83,3 +83,75 @@ def cat_pair(cfg, J=None):
            "n_a2": D.Operator.local(dims, a2, D.op_num(dims[a2])),
            "parity_a1": D.Operator.local(dims, a1, D.op_parity(dims[a1]))}
     return DenseSystem(dims, H, Ls, observables=obs, init=[D.fock(N, 0) for N in dims])
+
+
+def transmon_eigenbasis(ec, ej, K, n_cut=500, tie=1e-9):
+    """Sec. VII, numerical experiment: diagonalise the transmon alone,
+    4 Ec n^2 - Ej cos(phi) on the charges |n| <= n_cut (cos(phi) cut open at both
+    ends, ng = 0), keep the K lowest eigenstates Psi_alpha(n) and write
+    [n_t]_{alpha beta} = sum_n Psi_alpha(n) n Psi_beta(n).
+
+    Readings: the eigenstates are taken with definite charge parity (n -> -n), so
+    that the exactly degenerate pairs above the well give a unique basis; within a
+    pair (energies equal to `tie` relative to their size) the even state comes first; each
+    eigenvector's largest component over n >= 0 (the first such n on ties) is
+    positive.  Returns (energies ascending, n_t, Psi as columns over n)."""
+    n = np.arange(-n_cut, n_cut + 1, dtype=np.float64)
+    N = n.size
+    H = np.diag(4.0 * ec * n * n) - 0.5 * ej * (np.eye(N, k=1) + np.eye(N, k=-1))
+    c = n_cut
+    # parity sectors as charge-basis columns
+    Pe = np.zeros((N, n_cut + 1))
+    Po = np.zeros((N, n_cut))
+    Pe[c, 0] = 1.0
+    for m in range(1, n_cut + 1):
+        Pe[c + m, m] = Pe[c - m, m] = np.sqrt(0.5)
+        Po[c + m, m - 1] = np.sqrt(0.5)
+        Po[c - m, m - 1] = -np.sqrt(0.5)
+    states = []
+    for P, parity in ((Pe, 0), (Po, 1)):
+        w, v = np.linalg.eigh(P.T @ H @ P)
+        for j in range(w.size):
+            states.append((w[j], parity, P @ v[:, j]))
+    states.sort(key=lambda st: st[0])
+    # even before odd inside a degenerate pair
+    i = 0
+    while i + 1 < len(states):
+        a, b = states[i], states[i + 1]
+        if abs(a[0] - b[0]) <= tie * max(abs(a[0]), abs(b[0])) and a[1] > b[1]:
+            states[i], states[i + 1] = b, a
+        i += 1
+    states = states[:K]
+    E = np.array([st[0] for st in states])
+    Psi = np.stack([st[2] for st in states], axis=1)
+    for j in range(K):
+        half = Psi[c:, j]
+        k = int(np.argmax(np.abs(half)))
+        if half[k] < 0:
+            Psi[:, j] = -Psi[:, j]
+    nt = Psi.T @ (n[:, None] * Psi)
+    return E, nt, Psi
+
+
+def transmon_eig(cfg, nsteps, f_table):
+    """Transmon x resonator with the transmon in its eigenbasis (Sec. VII,
+    numerical experiment): H0 = diag(eps_alpha - eps_0) + w_r a^dag a
+    + g n_t (a + a^dag), drive f(t_n) (a + a^dag), L = sqrt(kappa) a; observables
+    N_t = Tr(b^dag b rho) with b^dag b = diag(alpha) and N_c = Tr(a^dag a rho);
+    start in transmon eigenstate 0 x vacuum."""
+    Rt, Rr = cfg["R"]
+    K, Nr = 2 ** Rt, 2 ** Rr
+    dims = (K, Nr)
+    ec = cfg["ec"]
+    ej = cfg["ej_over_ec"] * ec
+    g = cfg["g_over_ec"] * ec
+    E, nt, _ = transmon_eigenbasis(ec, ej, K, cfg.get("n_cut", 500))
+    a, ad = D.op_a(Nr), D.op_adag(Nr)
+    Ht = np.diag(E - E[0]).astype(np.complex128)
+    ntc = nt.astype(np.complex128)
+    H0 = D.Operator(dims, [(1.0, {0: Ht}), (cfg["wr"], {1: D.op_num(Nr)}), (g, {0: ntc, 1: a}),
+                           (g, {0: ntc, 1: ad})])
+    H1 = D.Operator(dims, [(1.0, {1: a}), (1.0, {1: ad})])
+    Ls = [D.Operator.local(dims, 1, a, np.sqrt(cfg["kappa"]))]
+    obs = {"n_c": D.Operator.local(dims, 1, D.op_num(Nr)), "n_t": D.Operator.local(dims, 0, D.op_num(K))}
+    return DenseSystem(dims, H0, Ls, H1=H1, f_table=f_table, observables=obs, init=[D.fock(K, 0), D.fock(Nr, 0)])
