@@ -15,6 +15,8 @@ Systems (all from the paper's applications, Sec. VI and Sec. VII):
   transmon      transmon in the charge basis (128 charge states) x resonator
                 (N = 1024), coupling g n_t (a + a^dag), ramped drive
                 eps(t) cos(w_r t)(a + a^dag), L = sqrt(kappa) a.
+  transmon_eig  the same transmon x resonator with the transmon in its
+                eigenbasis (|n| <= 500 charges diagonalised, lowest 2^5 states).
   cat_pair      two storage cats (N = 256) each with a buffer (N = 16),
                 three-wave mixing g2 (a^2 b^dag + h.c.), buffer drive, beam
                 splitter J (a1^dag a2 + h.c.), 16 variants of J.
@@ -41,6 +43,12 @@ _CONFIGS = {
     # Units: angular frequency in rad/ns (GHz * 2 pi), time in ns.
     "transmon": dict(
         kind="transmon", R=[7, 10], ec=2 * np.pi * 0.28, ej_over_ec=50.0, ng=0.0,
+        wr=2 * np.pi * 7.5, g_over_ec=0.5, kappa=2 * np.pi * 0.02, eps_over_kappa=40.0,
+        ramp_kappa_t=200.0, dt=2e-6, steps=10000, tol=1e-12, chi_max=128, chi_mu_max=16,
+        record_every=100, check=dict(R=[5, 6]),
+    ),
+    "transmon_eig": dict(
+        kind="transmon_eig", R=[5, 10], ec=2 * np.pi * 0.28, ej_over_ec=50.0, n_cut=500,
         wr=2 * np.pi * 7.5, g_over_ec=0.5, kappa=2 * np.pi * 0.02, eps_over_kappa=40.0,
         ramp_kappa_t=200.0, dt=2e-6, steps=10000, tol=1e-12, chi_max=128, chi_mu_max=16,
         record_every=100, check=dict(R=[5, 6]),

@@ -82,6 +82,87 @@ def build_transmon(ctx, cfg, nsteps=None):
     return Built(s, ops, init, obs, cfg, f)
 
 
+def transmon_levels(ec, ej, K, n_cut=500, tie=1e-9):
+    """Transmon eigenbasis of Sec. VII (numerical experiment) for the operator
+    builder: the K lowest eigenstates of 4 Ec n^2 - Ej cos(phi) on the charges
+    |n| <= n_cut (ng = 0, cos(phi) cut open), and the charge operator in that basis.
+
+    Found per charge-parity sector as two tridiagonal chains:
+      even |0>, (|m> + |-m>)/sqrt 2: diagonal 4 Ec m^2, coupling -Ej/sqrt 2 between
+        m = 0 and 1, -Ej/2 further on;
+      odd (|m> - |-m>)/sqrt 2, m >= 1: diagonal 4 Ec m^2, couplings -Ej/2.
+    n is odd under n -> -n, so [n_t] joins an even state e and an odd state o only:
+    <e| n |o> = sum_{m >= 1} e_m o_m m.  Conventions: within a degenerate pair
+    (energies equal to `tie` relative) the even state comes first, and each state's
+    largest charge amplitude over n >= 0 is positive.
+    Returns (energies ascending, n_t as a real K x K array)."""
+    from scipy.linalg import eigh_tridiagonal
+
+    m = np.arange(n_cut + 1, dtype=np.float64)
+    d_even = 4.0 * ec * m * m
+    off_even = np.full(n_cut, -0.5 * ej)
+    off_even[0] = -ej / np.sqrt(2.0)
+    we, ve = eigh_tridiagonal(d_even, off_even)
+    wo, vo = eigh_tridiagonal(d_even[1:], np.full(n_cut - 1, -0.5 * ej))
+    # charge amplitudes over n = 0..n_cut of every sector state
+    amp_e = ve.copy()
+    amp_e[1:, :] *= np.sqrt(0.5)
+    amp_o = np.zeros((n_cut + 1, wo.size))
+    amp_o[1:, :] = vo * np.sqrt(0.5)
+    levels = [(we[j], 0, j) for j in range(we.size)] + [(wo[j], 1, j) for j in range(wo.size)]
+    levels.sort(key=lambda t: t[0])
+    for i in range(len(levels) - 1):
+        a, b = levels[i], levels[i + 1]
+        if a[1] == 1 and b[1] == 0 and abs(a[0] - b[0]) <= tie * max(abs(a[0]), abs(b[0])):
+            levels[i], levels[i + 1] = b, a
+    levels = levels[:K]
+    energies = np.array([t[0] for t in levels])
+    vecs = []
+    for _, parity, j in levels:
+        amp = amp_e[:, j] if parity == 0 else amp_o[:, j]
+        k = int(np.argmax(np.abs(amp)))
+        sgn = -1.0 if amp[k] < 0 else 1.0
+        vecs.append((parity, sgn * (ve[:, j] if parity == 0 else vo[:, j])))
+    nt = np.zeros((K, K))
+    for a, (pa, va) in enumerate(vecs):
+        for b, (pb, vb) in enumerate(vecs):
+            if pa == 0 and pb == 1:
+                nt[a, b] = nt[b, a] = float(np.dot(va[1:] * m[1:], vb))
+    return energies, nt
+
+
+def build_transmon_eig(ctx, cfg, nsteps=None):
+    """Transmon x resonator with the transmon in its eigenbasis (Sec. VII): the
+    transmon mode carries the 2^R_t lowest transmon states; H0 = diag(eps - eps_0)
+    + w_r a^dag a + g n_t (a + a^dag), drive f(t_n)(a + a^dag), L = sqrt(kappa) a.
+    Observables N_t = Tr(b^dag b rho) with b^dag b = diag(alpha) and N_c."""
+    Rt, Rr = cfg["R"]
+    K = 2 ** Rt
+    ec = cfg["ec"]
+    ej = cfg["ej_over_ec"] * ec
+    g = cfg["g_over_ec"] * ec
+    E, nt = transmon_levels(ec, ej, K, cfg.get("n_cut", 500))
+    s = Q.System(ctx, [Rt, Rr])
+    Ht = np.diag(E - E[0]).astype(np.complex128)
+    ntc = nt.astype(np.complex128)
+    ops = {}
+    ops["H0"] = s.op([
+        (1.0, [(0, Q.F_DENSE, Ht)]),
+        (cfg["wr"], [(1, Q.F_NUM)]),
+        (g, [(0, Q.F_DENSE, ntc), (1, Q.F_A)]),
+        (g, [(0, Q.F_DENSE, ntc), (1, Q.F_ADAG)]),
+    ])
+    ops["H1"] = s.op([(1.0, [(1, Q.F_A)]), (1.0, [(1, Q.F_ADAG)])])
+    n = nsteps if nsteps is not None else cfg["steps"]
+    f = inputs.transmon_drive_table(cfg, n)
+    s.set_hamiltonian(ops["H0"], ops["H1"], f)
+    ops["L"] = s.op([(np.sqrt(cfg["kappa"]), [(1, Q.F_A)])])
+    s.add_jump(ops["L"])
+    obs = {"n_c": s.op([(1.0, [(1, Q.F_NUM)])]), "n_t": s.op([(1.0, [(0, Q.F_NUM)])])}
+    init = [vacuum(K), vacuum(2 ** Rr)]  # transmon eigenstate 0 x cavity vacuum
+    return Built(s, ops, init, obs, cfg, f)
+
+
 def build_cat_pair(ctx, cfg, J=None):
     Rb1, Ra1, Ra2, Rb2 = cfg["R"][1], cfg["R"][0], cfg["R"][2], cfg["R"][3]
     s = Q.System(ctx, [Rb1, Ra1, Ra2, Rb2])
@@ -113,4 +194,6 @@ def build(ctx, cfg, **kw):
         return build_transmon(ctx, cfg, **kw)
     if kind == "cat_pair":
         return build_cat_pair(ctx, cfg, **kw)
+    if kind == "transmon_eig":
+        return build_transmon_eig(ctx, cfg, **kw)
     raise ValueError(kind)

@@ -7,7 +7,8 @@ absolute of the dense FP64 oracle (the truncated-form tolerance).
   dt = 5e-4 (recorded before the explicit step's instability takes over, and the
   stable twin dt = 1e-4 over a longer window, in both precision forms);
 * the second-order Kraus scheme on the N = 32 cat;
-* transmon x resonator at 32 charge states x 64 Fock levels with the ramped drive;
+* transmon x resonator at 32 charge states x 64 Fock levels with the ramped drive,
+  and with the transmon in its eigenbasis (32 lowest states);
 * the two coupled cats with buffers at (N_b, N_a, N_a, N_b) = (4, 8, 8, 4).
 """
 import numpy as np
@@ -74,6 +75,22 @@ def test_transmon_check_size():
             D.fock(2 ** cfg["R"][1], 0)]
     ds = OS.transmon(cfg, nsteps, b.f_table, init)
     worst = _compare(b, ds, dt, nsteps, 5, ["n_c", "n_t2"])
+    assert max(worst.values()) < 1e-6, worst
+    c.close()
+
+
+def test_transmon_eigenbasis_check_size():
+    """Sec. VII's construction: the transmon in its own eigenbasis (32 lowest states of
+    |n| <= 500 charges, dense factors) x 64 Fock levels with the ramped drive."""
+    cfg = inputs.config("transmon_eig")
+    cfg.update(cfg.pop("check"))  # 32 transmon states x 64 Fock levels
+    nsteps = 20
+    dt = 2e-5
+    cfg["dt"] = dt
+    c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])
+    b = systems.build(c, cfg, nsteps=nsteps)
+    ds = OS.transmon_eig(cfg, nsteps, b.f_table)
+    worst = _compare(b, ds, dt, nsteps, 5, ["n_c", "n_t"])
     assert max(worst.values()) < 1e-6, worst
     c.close()
 
