@@ -155,3 +155,27 @@ def transmon_eig(cfg, nsteps, f_table):
     Ls = [D.Operator.local(dims, 1, a, np.sqrt(cfg["kappa"]))]
     obs = {"n_c": D.Operator.local(dims, 1, D.op_num(Nr)), "n_t": D.Operator.local(dims, 0, D.op_num(K))}
     return DenseSystem(dims, H0, Ls, H1=H1, f_table=f_table, observables=obs, init=[D.fock(K, 0), D.fock(Nr, 0)])
+
+
+def z_gate(cfg, init):
+    """Z gate on a cat qubit with its buffer (Sec. VI, Eq. cb and Eq. Hz), modes
+    [a, b]: H = g2 (a^dag^2 b + a^2 b^dag) + eps_d (b + b^dag) + eps_Z (a + a^dag),
+    L_b = sqrt(kappa_b) b (+ sqrt(kappa_a) a).  Parameters from the product's
+    parameter set; `init` is the pair of mode vectors."""
+    from paper_2605_27515_gb300 import inputs
+
+    Ra, Rb = cfg["R"]
+    Na, Nb = 2 ** Ra, 2 ** Rb
+    dims = (Na, Nb)
+    zp = inputs.z_gate_params(cfg)
+    g2 = cfg["g2"]
+    A, Ad, B, Bd = D.op_a(Na), D.op_adag(Na), D.op_a(Nb), D.op_adag(Nb)
+    H = D.Operator(dims, [(g2, {0: Ad @ Ad, 1: B}), (g2, {0: A @ A, 1: Bd}), (zp["eps_d"], {1: B}),
+                          (zp["eps_d"], {1: Bd}), (zp["eps_z"], {0: A}), (zp["eps_z"], {0: Ad})])
+    Ls = [D.Operator.local(dims, 1, B, np.sqrt(cfg["kb"]))]
+    if cfg.get("ka", 0.0) > 0.0:
+        Ls.append(D.Operator.local(dims, 0, A, np.sqrt(cfg["ka"])))
+    obs = {"parity_a": D.Operator.local(dims, 0, D.op_parity(Na)), "n_a": D.Operator.local(dims, 0, D.op_num(Na)),
+           "n_b": D.Operator.local(dims, 1, D.op_num(Nb))}
+    return DenseSystem(dims, H, Ls, observables=obs, init=init)
+

@@ -17,6 +17,10 @@ Systems (all from the paper's applications, Sec. VI and Sec. VII):
                 eps(t) cos(w_r t)(a + a^dag), L = sqrt(kappa) a.
   transmon_eig  the same transmon x resonator with the transmon in its
                 eigenbasis (|n| <= 500 charges diagonalised, lowest 2^5 states).
+  z_gate        memory cat (N_a = 2^R_a, alpha^2 = N_a / 3) with a lossy buffer
+                (N_b = 16), g2 = 1, kappa_b = 10 g2, eps_Z = 4 g2^2 / (10 kappa_b),
+                theta = pi, kappa_a = 0 (Sec. VI numerical experiment), even-cat
+                start, T_Z = theta / (4 alpha eps_Z).
   cat_pair      two storage cats (N = 256) each with a buffer (N = 16),
                 three-wave mixing g2 (a^2 b^dag + h.c.), buffer drive, beam
                 splitter J (a1^dag a2 + h.c.), 16 variants of J.
@@ -52,6 +56,11 @@ _CONFIGS = {
         wr=2 * np.pi * 7.5, g_over_ec=0.5, kappa=2 * np.pi * 0.02, eps_over_kappa=40.0,
         ramp_kappa_t=200.0, dt=2e-6, steps=10000, tol=1e-12, chi_max=128, chi_mu_max=16,
         record_every=100, check=dict(R=[5, 6]),
+    ),
+    "z_gate": dict(
+        kind="z_gate", R=[9, 4], g2=1.0, kb=10.0, theta=float(np.pi), ka=0.0,
+        dt=1e-3, tol=1e-8, chi_max=64, chi_mu_max=16, record_every=100,
+        check=dict(R=[3, 2]),
     ),
     "cat_pair": dict(
         kind="cat_pair", R=[8, 4, 8, 4], alpha2=8.0, g2=0.2, kb=5.0, k1=1e-3, J=0.01,
@@ -122,3 +131,28 @@ def transmon_ground_charge(Nt: int, offset: int, ec: float, ej: float, ng: float
         H[j, j + 1] = H[j + 1, j] = -ej / 2
     w, v = np.linalg.eigh(H)
     return v[:, 0]
+
+
+def z_gate_params(cfg: dict) -> dict:
+    """Derived Z-gate parameters (Sec. VI): alpha^2 = N_a / 3, eps_d = -g2 alpha^2,
+    eps_Z = 4 g2^2 / (10 kappa_b), T_Z = theta / (4 alpha eps_Z), steps = T_Z / dt."""
+    Na = 2 ** cfg["R"][0]
+    alpha2 = cfg.get("alpha2", Na / 3.0)
+    alpha = float(np.sqrt(alpha2))
+    eps_z = 0.1 * 4.0 * cfg["g2"] ** 2 / cfg["kb"]
+    tz = cfg["theta"] / (4.0 * alpha * eps_z)
+    return dict(alpha2=alpha2, alpha=alpha, eps_d=-cfg["g2"] * alpha2, eps_z=eps_z, t_z=tz,
+                steps=int(round(tz / cfg["dt"])))
+
+
+def cat_vector(N: int, alpha: float, parity: int = +1) -> np.ndarray:
+    """Normalised cat |alpha> + parity |-alpha> in an N-level Fock space, from the
+    coherent amplitudes alpha^n / sqrt(n!) (each coherent part truncated)."""
+    c = np.zeros(N, dtype=np.complex128)
+    c[0] = 1.0
+    for n in range(1, N):
+        c[n] = c[n - 1] * alpha / np.sqrt(n)
+    sign = (-1.0) ** np.arange(N)
+    v = c + parity * sign * c
+    return v / np.linalg.norm(v)
+

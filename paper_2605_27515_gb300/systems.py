@@ -163,6 +163,34 @@ def build_transmon_eig(ctx, cfg, nsteps=None):
     return Built(s, ops, init, obs, cfg, f)
 
 
+def build_z_gate(ctx, cfg):
+    """Z gate on a cat qubit with its buffer (Sec. VI, Eq. cb and Eq. Hz), modes
+    [a (memory), b (buffer)]: H = g2 (a^dag^2 b + a^2 b^dag) + eps_d (b + b^dag)
+    + eps_Z (a + a^dag), L_b = sqrt(kappa_b) b (and sqrt(kappa_a) a when kappa_a > 0);
+    start in the even cat x buffer vacuum.  Observables: memory parity, photon
+    numbers."""
+    Ra, Rb = cfg["R"]
+    zp = inputs.z_gate_params(cfg)
+    g2 = cfg["g2"]
+    s = Q.System(ctx, [Ra, Rb])
+    a, b = 0, 1
+    ops = {"H": s.op([
+        (g2, [(a, Q.F_ADAG, 2), (b, Q.F_A)]), (g2, [(a, Q.F_A, 2), (b, Q.F_ADAG)]),
+        (zp["eps_d"], [(b, Q.F_A)]), (zp["eps_d"], [(b, Q.F_ADAG)]),
+        (zp["eps_z"], [(a, Q.F_A)]), (zp["eps_z"], [(a, Q.F_ADAG)]),
+    ])}
+    s.set_hamiltonian(ops["H"])
+    ops["Lb"] = s.op([(np.sqrt(cfg["kb"]), [(b, Q.F_A)])])
+    s.add_jump(ops["Lb"])
+    if cfg.get("ka", 0.0) > 0.0:
+        ops["La"] = s.op([(np.sqrt(cfg["ka"]), [(a, Q.F_A)])])
+        s.add_jump(ops["La"])
+    obs = {"parity_a": s.op([(1.0, [(a, Q.F_PARITY)])]), "n_a": s.op([(1.0, [(a, Q.F_NUM)])]),
+           "n_b": s.op([(1.0, [(b, Q.F_NUM)])])}
+    init = [inputs.cat_vector(2 ** Ra, zp["alpha"], +1), vacuum(2 ** Rb)]
+    return Built(s, ops, init, obs, cfg)
+
+
 def build_cat_pair(ctx, cfg, J=None):
     Rb1, Ra1, Ra2, Rb2 = cfg["R"][1], cfg["R"][0], cfg["R"][2], cfg["R"][3]
     s = Q.System(ctx, [Rb1, Ra1, Ra2, Rb2])
@@ -196,4 +224,6 @@ def build(ctx, cfg, **kw):
         return build_cat_pair(ctx, cfg, **kw)
     if kind == "transmon_eig":
         return build_transmon_eig(ctx, cfg, **kw)
+    if kind == "z_gate":
+        return build_z_gate(ctx, cfg)
     raise ValueError(kind)
