@@ -2,7 +2,7 @@
 
 Untruncated FP64 form: observables within 1e-10 of the dense oracle.
 Truncated form (stated tolerance): within 1e-6 absolute (photon number, parity,
-fidelity), the bar the spec sets for the truncated path.
+fidelity), the bar for the truncated path.
 """
 import numpy as np
 import pytest
