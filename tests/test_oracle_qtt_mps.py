@@ -179,6 +179,25 @@ def test_untruncated_mps_step_equals_dense(Rs):
         np.testing.assert_allclose(M.density(cores), rho, atol=1e-12)
 
 
+def test_untruncated_second_order_mps_step_equals_dense():
+    """The purified MPS step with the 1 + 2l + l^2 second-order branches stacked on
+    the purification leg reproduces the dense second-order map (Sec. V.B)."""
+    dims, H, Ls, vecs = _system([2, 2], 6)
+    h = 0.02
+    U = D.u1(H, Ls, h).dense()
+    He = D.h_eff(H, Ls).dense()
+    Ld = [L.dense() for L in Ls]
+    Ks = [U - 0.5 * h * h * He @ He] + [np.sqrt(h / 2) * U @ L for L in Ld] + [np.sqrt(h / 2) * L @ U for L in Ld]
+    Ks += [h / np.sqrt(2) * A @ B for A in Ld for B in Ld]
+    W = M.kraus_mpos(Ks, 4)
+    cores = M.product_state(vecs, [2, 2])
+    rho = D.pure(D.product_vector(vecs))
+    for _ in range(4):
+        cores, info = M.kraus_step(cores, W, 1e-28, 10 ** 6, 10 ** 6)
+        rho = D.kraus_step(rho, H, Ls, h, order=2)
+        np.testing.assert_allclose(M.density(cores), rho, atol=1e-12)
+
+
 def test_purification_truncation_keeps_top_eigenvalues():
     """Sec. IV.A: the kept s_i^2 are the largest eigenvalues of rho."""
     dims, H, Ls, vecs = _system([3], 9)
