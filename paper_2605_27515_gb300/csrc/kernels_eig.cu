@@ -626,9 +626,9 @@ cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void
   }
   size_t want = eig_smem_bytes<R>(e.n_max);
   int dyn = (int)(want <= EIG_SMEM_LIMIT ? want : EIG_SMEM_LIMIT);
-  // FP64: the DFMA pipe bounds the rotations, a few warps keep it busy.  Double-
-  // float: long dependent FP32 chains per rotation, so a full CTA of warps hides
-  // their latency.
+  // FP64: a few warps suffice (ncu shows the solve waiting on its round barriers
+  // and the DFMA pipe, not on issue slots).  Double-float: long dependent FP32
+  // chains per rotation, so a full CTA of warps hides their latency.
   constexpr bool wide = std::is_same<R, df64>::value;
   if (e.n_max <= 24)
     k_eig<R, 128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
