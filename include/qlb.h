@@ -100,6 +100,10 @@ qlb_status qlb_ctx_stream(qlb_ctx* ctx, void** stream);
 qlb_status qlb_synchronize(qlb_ctx* ctx);
 /* Device bytes currently held by the context. */
 qlb_status qlb_ctx_memory(qlb_ctx* ctx, size_t* bytes);
+/* Number of device allocations the context has made since it was created (every
+ * buffer of its systems, ops and states, and per-call temporaries).  Lets a caller
+ * check that a call allocated nothing.  The paper has no counterpart. */
+qlb_status qlb_ctx_alloc_count(qlb_ctx* ctx, int64_t* n);
 
 /* ------------------------------------------------------------------ systems */
 
@@ -209,18 +213,20 @@ qlb_status qlb_trace(qlb_state* st, double* out);
 qlb_status qlb_purity(qlb_state* st, double* out);
 /* Tr rho^2 like qlb_purity, but allocating no device memory.  The paper has no
  * counterpart: this call exists for callers that must not allocate while they
- * ask, e.g. code running inside CUDA stream capture (where cudaMalloc is not
- * allowed), code whose device memory belongs to another allocator with a fixed
+ * ask, e.g. code whose device memory belongs to another allocator with a fixed
  * budget, or monitoring loops that cannot pay for the device-wide
  * synchronisation of cudaFree.  The Gram matrix and the sums live in a fixed
  * scratch array inside the library's device image (about 256 KB, held by every
  * GPU that loads the library until the process exits); it serves purification
- * ranks chi_mu <= 128 and returns QLB_EINVAL with a message for larger ones.
- * The first call on a device looks up that array's device address (no
- * allocation); make that first call before any stream capture.  All calls share
- * the one array, so calls that overlap on the GPU (other host threads, other
- * streams) race; results are written, never accumulated, so a previous call's
- * contents do not matter.  Synchronous; out receives the purity. */
+ * ranks chi_mu <= 128 and returns QLB_EINVAL with a message for larger ones
+ * (qlb_create caps chi_mu_max at 128, so no state of this library reaches that
+ * branch today).  The first call on a device looks up that array's device
+ * address with that device current (no allocation).  All calls share the one
+ * array, so calls that overlap on the GPU (other host threads, other streams)
+ * race; results are written, never accumulated, so a previous call's contents do
+ * not matter.  The call is synchronous: it reads the bond dimensions back and
+ * waits for the state's stream, so it cannot run inside CUDA stream capture.
+ * out receives the purity. */
 qlb_status qlb_purity_noalloc(qlb_state* st, double* out);
 /* [chi_mu, chi_1, ..., chi_{L-1}] (n_out = L). */
 qlb_status qlb_bond_dims(qlb_state* st, int* out, int cap, int* n_out);
@@ -261,6 +267,18 @@ qlb_status qlb_profile_enable(qlb_ctx* ctx, int on);
 qlb_status qlb_profile_read(qlb_ctx* ctx, int kclass, double* ms, int64_t* launches, double* flops,
                             double* bytes);
 qlb_status qlb_profile_reset(qlb_ctx* ctx);
+/* Eigen-solver counters of the context since the last qlb_profile_reset, kept
+ * whether or not profiling is on (also inside captured step graphs):
+ * out5[0] solves, out5[1] Jacobi sweeps plus QL passes, out5[2] sum of the
+ * runtime matrix sizes n, out5[3] sum of the kept counts k, out5[4] solves that
+ * reached the sweep (or QL iteration) limit.  Synchronises the device. */
+qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out5);
+
+/* Measured fused multiply-add throughput of device `device` in TFLOP/s:
+ * kind 0 = FP64, kind 1 = FP32 (independent FMA chains over every SM, timed with
+ * CUDA events, best of three ~20 ms launches).  The denominators of the
+ * truncation solvers' roofline.  Allocates a few KB for the duration of the call. */
+qlb_status qlb_measure_peak(int device, int kind, double* tflops);
 
 #ifdef __cplusplus
 }

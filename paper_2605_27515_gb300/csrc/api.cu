@@ -121,13 +121,14 @@ using namespace qlb;
 
 qlb_op::~qlb_op() {
   for (auto p : owned) dev_free(nullptr, p);
+  for (auto p : step_core) dev_free(nullptr, p);
 }
 
 qlb_state::~qlb_state() {
   if (stream) cudaStreamSynchronize(stream);
   if (graph) cudaGraphExecDestroy(graph);
   for (auto p : site) dev_free(nullptr, p);
-  for (auto p : {X, Mb, G, Cin, Cout, T1, T2, T3, eigw}) dev_free(nullptr, p);
+  for (auto p : {X, Mb, G, Cin, Cout, T1, T2, T3, eigw, oE0, oE1, oY, oZ}) dev_free(nullptr, p);
   dev_free(nullptr, d_lam);
   dev_free(nullptr, d_stats);
   dev_free(nullptr, d_err);
@@ -194,6 +195,15 @@ QLB_API qlb_status qlb_create(const qlb_options* opt, qlb_ctx** out) {
     return QLB_EDEVICE;
   }
   init_kernel_attributes();
+  {
+    qlb_status st = dev_alloc(c, (void**)&c->d_solver, sizeof(double) * 8);
+    if (st == QLB_OK && cudaMemset(c->d_solver, 0, sizeof(double) * 8) != cudaSuccess) st = QLB_EDEVICE;
+    if (st) {
+      cudaStreamDestroy(c->stream);
+      delete c;
+      return st;
+    }
+  }
   // keep freed blocks in the device pool for reuse instead of returning them to
   // the driver between allocations (process-local allocator setting)
   cudaMemPool_t pool;
@@ -210,6 +220,7 @@ QLB_API void qlb_destroy(qlb_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   dev_free(ctx, ctx->d_prof);
+  dev_free(ctx, ctx->d_solver);
   cudaStreamDestroy(ctx->stream);
   // buffers still held by systems, ops or states of this context no longer
   // report to it when they are freed later
@@ -252,6 +263,12 @@ QLB_API qlb_status qlb_synchronize(qlb_ctx* ctx) {
 QLB_API qlb_status qlb_ctx_memory(qlb_ctx* ctx, size_t* bytes) {
   CHECK_ARG(ctx && bytes, "null argument");
   *bytes = ctx->mem_held;
+  return QLB_OK;
+}
+
+QLB_API qlb_status qlb_ctx_alloc_count(qlb_ctx* ctx, int64_t* n) {
+  CHECK_ARG(ctx && n, "null argument");
+  *n = ctx->n_allocs;
   return QLB_OK;
 }
 
@@ -658,7 +675,22 @@ QLB_API qlb_status qlb_step(qlb_state* st, double dt, int64_t n) {
 QLB_API qlb_status qlb_expectation(qlb_state* st, const qlb_op* O, double* out) {
   CHECK_ARG(st && O && out, "null argument");
   CHECK_ARG(O->sys == st->sys, "operator belongs to another system");
-  return expectation_mpo(st, O->mpo, out);
+  qlb_op* op = const_cast<qlb_op*>(O);
+  if (op->step_core.empty()) {
+    qlb_ctx* ctx = st->sys->ctx;
+    std::vector<zd*> c;
+    qlb_status s = mpo_step_layout(ctx, op->mpo, c, ctx->stream);
+    if (s == QLB_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+      set_error("step-layout conversion of the operator failed");
+      s = QLB_EDEVICE;
+    }
+    if (s) {
+      for (auto p : c) dev_free(ctx, p);
+      return s;
+    }
+    op->step_core = c;
+  }
+  return expectation_mpo(st, op->step_core, op->mpo.D, out);
 }
 
 QLB_API qlb_status qlb_fidelity(qlb_state* st, const double* const* target, double* out) {
@@ -679,10 +711,13 @@ QLB_API qlb_status qlb_fidelity(qlb_state* st, const double* const* target, doub
     if ((s = dev_alloc(ctx, (void**)&W.core[i], sizeof(zd) * n))) break;
     k_projector_core<<<nblk(n), 256, 0, ctx->stream>>>(P[i], D[i], D[i + 1], W.core[i]);
   }
+  std::vector<zd*> Ws;
+  if (!s) s = mpo_step_layout(ctx, W, Ws, ctx->stream);
   cudaStreamSynchronize(ctx->stream);
   for (auto p : P) dev_free(ctx, p);
   double r[2] = {0, 0};
-  if (!s) s = expectation_mpo(st, W, r);
+  if (!s) s = expectation_mpo(st, Ws, W.D, r);
+  for (auto p : Ws) dev_free(ctx, p);
   mpo_clear(ctx, W);
   if (s) return s;
   *out = r[0];
@@ -881,5 +916,16 @@ QLB_API qlb_status qlb_profile_reset(qlb_ctx* ctx) {
     ctx->prof_launch[k] = 0;
   }
   if (ctx->d_prof) QLB_CUDA_TRY(cudaMemset(ctx->d_prof, 0, sizeof(double) * 2 * QLB_K_COUNT));
+  QLB_CUDA_TRY(cudaDeviceSynchronize());
+  if (ctx->d_solver) QLB_CUDA_TRY(cudaMemset(ctx->d_solver, 0, sizeof(double) * 8));
+  return QLB_OK;
+}
+
+QLB_API qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out5) {
+  CHECK_ARG(ctx && out5, "null argument");
+  QLB_CUDA_TRY(cudaDeviceSynchronize());
+  double h[8] = {0};
+  if (ctx->d_solver) QLB_CUDA_TRY(cudaMemcpy(h, ctx->d_solver, sizeof(h), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 5; i++) out5[i] = h[i];
   return QLB_OK;
 }

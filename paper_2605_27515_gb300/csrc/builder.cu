@@ -38,6 +38,7 @@ qlb_status dev_alloc(qlb_ctx* ctx, void** p, size_t bytes) {
     return QLB_ENOMEM;
   }
   ctx->mem_held += bytes;
+  ctx->n_allocs++;
   g_alloc_sizes()[*p] = std::make_pair(bytes, ctx);
   return QLB_OK;
 }

@@ -7,10 +7,15 @@
 // and (c, s) the real symmetric Schur pair of [[G_pp, |G_pq|], [|G_pq|, G_qq]]
 // (Golub & Van Loan, sym.schur2); G <- J^dag G J, V <- V J.  A pair is skipped
 // when |G_pq| <= n eps sqrt(|G_pp G_qq|) (the relative criterion that keeps small
-// eigenvalues of a Gram matrix accurate) or below an absolute floor of
-// eps Tr G / 10, under the rounding already carried by the Gram matrix itself;
-// a sweep with no rotation ends the solve.  At the sweep limit the solve is
-// accepted when the off-diagonal norm left is below n eps Tr G.
+// eigenvalues of a Gram matrix accurate), below an absolute floor of eps Tr G / 10
+// (under the rounding already carried by the Gram matrix itself), or when both
+// G_pp and G_qq are at most n eps Tr G: two directions that are both numerically
+// zero hold nothing a rotation between them could resolve, and rotating them only
+// trades rounding noise back and forth until the sweep limit.  Pairs of a real
+// direction with a numerically zero one are still rotated, so real weight is
+// never mixed into a direction the truncation may drop.  A sweep with no rotation
+// ends the solve.  At the sweep limit the solve is accepted when the off-diagonal
+// norm left is below n eps Tr G.
 //
 // Each round has three barriers: rotation parameters, row update (J^dag G), and
 // column update (G J, V J) which also writes the annihilated entries as exact
@@ -127,6 +132,11 @@ __device__ void eig_finish(const EigDesc& e, int* d, int n, const double* lam, c
     }
     if (e.lam)
       for (int i = 0; i < n; i++) e.lam[i] = s_w[i];
+    if (e.solver_stats) {
+      atomicAdd(e.solver_stats + 0, 1.0);
+      atomicAdd(e.solver_stats + 2, (double)n);
+      atomicAdd(e.solver_stats + 3, (double)k);
+    }
     if (e.err) {
       if (unconverged) atomicOr(e.err, 1);
       if (*s_bad || !isfinite(total)) atomicOr(e.err, 2);
@@ -202,6 +212,8 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
   }
   __syncthreads();
   const R abs_thr = s_thr;
+  // both diagonals at or below this: a pair of numerically zero directions
+  const R zero_floor = to_r<R>(Eps<R>::v * (double)n * s_tr);
   // relative floor: rounding in the row/column updates leaves off-diagonals of
   // order n eps sqrt(G_pp G_qq); asking for less would rotate noise forever
   const R rel_tol = to_r<R>(Eps<R>::v * (double)(n > 8 ? n : 8));
@@ -228,7 +240,8 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
           R a = Gs[(long)p * np + p].re, b = Gs[(long)q * np + q].re;
           cx<R> gpq = Gs[(long)p * np + q];
           R x = sqrt(cabs2(gpq));
-          if (x > rel_tol * sqrt(fabs(a * b)) && x > abs_thr && x > zero) {
+          const bool both_zero = fabs(a) <= zero_floor && fabs(b) <= zero_floor;
+          if (!both_zero && x > rel_tol * sqrt(fabs(a * b)) && x > abs_thr && x > zero) {
             R tau = (b - a) / (x + x);
             R t = fabs(tau) > to_r<R>(1e15) ? to_r<R>(0.5) / tau
                                             : (tau >= zero ? one : -one) / (fabs(tau) + sqrt(one + tau * tau));
@@ -291,7 +304,12 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
     if (nr == 0) break;
   }
   bool unconverged = false;
-  if (sweep >= e.max_sweeps) {
+  const bool at_limit = sweep >= e.max_sweeps;
+  if (e.solver_stats && tid == 0) {
+    atomicAdd(e.solver_stats + 1, (double)(at_limit ? e.max_sweeps : sweep + 1));
+    if (at_limit) atomicAdd(e.solver_stats + 4, 1.0);
+  }
+  if (at_limit) {
     // accept a solve whose remaining couplings are at the rounding level
     if (tid == 0) s_off = 0.0;
     __syncthreads();
@@ -371,6 +389,7 @@ __global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd*
   __shared__ int s_perm[512];
   __shared__ double s_w[512];
   __shared__ int s_k, s_bad;
+  __shared__ int s_pass_count;
   const double eps = 2.220446049250313e-16;
 
   const zd* G = (const zd*)e.G;
@@ -574,7 +593,15 @@ __global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd*
       }
     }
     __syncthreads();
-    if (s_done[b]) break;  // a finishing pass produces no rotations
+    if (s_done[b]) {  // a finishing pass produces no rotations
+      if (tid == 0) s_pass_count = t + 1;
+      break;
+    }
+  }
+  __syncthreads();
+  if (e.solver_stats && tid == 0) {
+    atomicAdd(e.solver_stats + 1, (double)(s_pass_count));
+    if (s_fail) atomicAdd(e.solver_stats + 4, 1.0);
   }
   if (prof && tid == 0) {
     atomicAdd(prof, flops + 8.0 * (double)n * (double)n_rot);

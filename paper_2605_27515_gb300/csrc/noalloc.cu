@@ -4,10 +4,11 @@
 // This variant runs the same Gram GEMM and reduction in a fixed scratch array that
 // lives in the library's own device image (a file-scope __device__ array), so it
 // never calls cudaMalloc or cudaFree.  That matters for callers that may not
-// allocate at that moment: code running inside CUDA stream capture (cudaMalloc is
-// not allowed there), callers whose device memory is owned by another allocator
-// with a fixed budget, and latency-sensitive monitoring loops that cannot afford
-// the device-wide synchronisation that cudaFree implies.
+// allocate at that moment: callers whose device memory is owned by another
+// allocator with a fixed budget, and latency-sensitive monitoring loops that
+// cannot afford the device-wide synchronisation that cudaFree implies.  The call
+// itself synchronises (it reads the bond dimensions back and waits for the
+// result), so it is not meant for use inside CUDA stream capture.
 
 #include <mutex>
 

@@ -135,6 +135,7 @@ struct EigDesc {
   double* total_weight; // optional: sum of all eigenvalues
   double* disc_stat;    // optional: running max of discarded relative weight
   int* err;             // error flags (bit 0: no convergence, bit 1: non-finite)
+  double* solver_stats; // optional counters (see qlb_ctx::d_solver)
 };
 
 // ------------------------------------------------------------------ error plumbing

@@ -50,6 +50,11 @@ struct qlb_ctx {
   qlb_options opt;
   cudaStream_t stream = nullptr;
   size_t mem_held = 0;
+  long long n_allocs = 0;  // device allocations made for this context so far
+  // eigen-solver counters, updated by every solve of the context's states (also
+  // inside captured graphs): [0] solves, [1] Jacobi sweeps / QL passes, [2] sum of
+  // runtime sizes n, [3] sum of kept counts k, [4] solves that hit the sweep limit
+  double* d_solver = nullptr;
   // profiling
   bool prof_on = false;
   struct PEv {
@@ -91,6 +96,7 @@ struct qlb_op {
   std::vector<qlb::DevTerm> terms;
   std::vector<qlb::zd*> owned;  // device dense factors owned by this op
   qlb::Mpo mpo;
+  std::vector<qlb::zd*> step_core;  // the MPO in step layout, made on first use by qlb_expectation
   double inf_norm_bound = 0.0;  // sum_t |c_t| prod_m ||F_m||_inf
   ~qlb_op();
 };
@@ -136,6 +142,9 @@ struct qlb_state {
   qlb::zd *X = nullptr, *Mb = nullptr, *G = nullptr, *Cin = nullptr, *Cout = nullptr;
   qlb::zd *T1 = nullptr, *T2 = nullptr, *T3 = nullptr, *eigw = nullptr;
   size_t nX = 0, nM = 0, nG = 0, nC = 0, nT = 0, nEw = 0;
+  // transfer-sweep buffers of the observables (grown on demand, reused by later calls)
+  qlb::zd *oE0 = nullptr, *oE1 = nullptr, *oY = nullptr, *oZ = nullptr;
+  size_t noE = 0, noY = 0, noZ = 0;
   double* d_lam = nullptr;
   double* d_stats = nullptr;  // [0] kept weight (mu), [1] total weight (mu), [2] max disc, [3] scratch
   int* d_err = nullptr;

@@ -167,8 +167,10 @@ static void prof_after(qlb_ctx* ctx, cudaStream_t sm, int kclass, cudaEvent_t a)
   ctx->prof_events.push_back({kclass, a, b});
 }
 
-// Opt-in trace for debugging (QLB_DEBUG_DUMP=<file>): after every launch of an
-// uncaptured step, append the dims array and the first entries of the output.
+#ifdef QLB_DEBUG_DUMP
+// Debug builds only (compiled with -DQLB_DEBUG_DUMP): with QLB_DEBUG_DUMP=<file> in
+// the environment, append the dims array and the first entries of the output after
+// every launch of an uncaptured step.
 static FILE* debug_file() {
   static FILE* f = nullptr;
   static bool init = false;
@@ -199,6 +201,10 @@ static void debug_dump(qlb_state* st, int tag, const void* out) {
   fwrite(buf.data(), sizeof(zd), 64, f);
   fflush(f);
 }
+#else
+static inline FILE* debug_file() { return nullptr; }
+static inline void debug_dump(qlb_state*, int, const void*) {}
+#endif
 
 static qlb_status gemm(qlb_state* st, GemmDesc& g) {
   qlb_ctx* ctx = st->sys->ctx;
@@ -219,6 +225,7 @@ static qlb_status eig(qlb_state* st, EigDesc& e) {
   cudaEvent_t a;
   prof_before(ctx, st->stream, QLB_K_EIG, &a);
   double* pf = ctx->prof_on ? ctx->d_prof + QLB_K_EIG : nullptr;
+  e.solver_stats = ctx->d_solver;
   // the mixed form runs the same Jacobi in double-float on the FP32 pipes
   cudaError_t r = st->prec == QLB_PREC_MIXED ? launch_eig<df64>(e, st->d_dims, st->stream, st->eigw, pf)
                                              : launch_eig<double>(e, st->d_dims, st->stream, st->eigw, pf);
@@ -995,114 +1002,117 @@ qlb_status truncate_pass(qlb_state* st) {
 
 // ------------------------------------------------------------------ observables
 
+// E[l'][l][0] = delta_{l' l} for l, l' < d[0] (trace over the purification index)
+__global__ void k_transfer_start(zd* E, const int* d, long cap) {
+  const long mu = d[0];
+  for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < mu * mu && x < cap; x += (long)gridDim.x * blockDim.x)
+    E[x] = mk<double>((x / mu) == (x % mu) ? 1.0 : 0.0, 0.0);
+}
+
+// Builder-layout MPO -> step layout [s'][a][s][b] in new device buffers.
+qlb_status mpo_step_layout(qlb_ctx* ctx, const Mpo& Wb, std::vector<zd*>& out, cudaStream_t sm) {
+  out.assign(Wb.L, nullptr);
+  for (int i = 0; i < Wb.L; i++) {
+    long n = (long)Wb.D[i] * 4 * Wb.D[i + 1];
+    qlb_status s = dev_alloc(ctx, (void**)&out[i], sizeof(zd) * n);
+    if (s) return s;
+    k_to_step_layout<<<nblk(n), 256, 0, sm>>>(Wb.core[i], Wb.D[i], Wb.D[i + 1], out[i]);
+  }
+  QLB_CUDA_TRY(cudaGetLastError());
+  return QLB_OK;
+}
+
 // Tr(O rho) by the transfer E[l'][l][a] (bra, ket, MPO bond):
 //   Y_l'[a][(s,r)] = sum_l E_l'[l][a] A[l][(s,r)]
 //   Z[(l',s')][(r,b)] = sum_{a,s} Y_l'[(a,s)][r] W_s'[(a,s)][b]
 //   E'[r'][(r,b)] = sum_{(l',s')} conj(A[(l',s')][r']) Z[(l',s')][(r,b)]
-// starting from E[mu'][mu][0] = delta (trace over the purification index).
-qlb_status expectation_mpo(qlb_state* st, const Mpo& Wb, double* out) {
+// starting from E[mu'][mu][0] = delta (trace over the purification index).  The
+// shapes are read from the state's device dims and the buffers belong to the
+// state (grown only when the op's MPO bonds need more), so a call allocates
+// nothing once the state has seen an op of this size, and it synchronises once,
+// for the result.
+qlb_status expectation_mpo(qlb_state* st, const std::vector<zd*>& W, const std::vector<int>& D, double* out) {
   qlb_ctx* ctx = st->sys->ctx;
   const int L = st->L;
-  std::vector<int> d;
-  qlb_status s;
-  if ((s = read_dims(st, d))) return s;
-  // op in step layout
-  std::vector<zd*> W(L, nullptr);
-  std::vector<zd*> bufs;
-  auto cleanup = [&]() {
-    for (auto p : W) dev_free(ctx, p);
-    for (auto p : bufs) dev_free(ctx, p);
-  };
-  for (int i = 0; i < L; i++) {
-    long n = (long)Wb.D[i] * 4 * Wb.D[i + 1];
-    if ((s = dev_alloc(ctx, (void**)&W[i], sizeof(zd) * n))) {
-      cleanup();
-      return s;
-    }
-    k_to_step_layout<<<nblk(n), 256, 0, st->stream>>>(Wb.core[i], Wb.D[i], Wb.D[i + 1], W[i]);
-  }
+  const std::vector<int>& hd = st->cap_state;
+  auto cap = [&](int i) { return (size_t)hd[SB(i)]; };
   size_t nE = 1, nY = 1, nZ = 1;
   for (int i = 0; i < L; i++) {
-    nE = std::max(nE, (size_t)d[i] * d[i] * Wb.D[i]);
-    nE = std::max(nE, (size_t)d[i + 1] * d[i + 1] * Wb.D[i + 1]);
-    nY = std::max(nY, (size_t)d[i] * Wb.D[i] * 2 * d[i + 1]);
-    nZ = std::max(nZ, (size_t)d[i] * 2 * d[i + 1] * Wb.D[i + 1]);
+    nE = std::max(nE, cap(i) * cap(i) * D[i]);
+    nE = std::max(nE, cap(i + 1) * cap(i + 1) * D[i + 1]);
+    nY = std::max(nY, cap(i) * D[i] * 2 * cap(i + 1));
+    nZ = std::max(nZ, cap(i) * 2 * cap(i + 1) * D[i + 1]);
   }
-  zd *E0, *E1, *Y, *Z;
-  if ((s = dev_alloc(ctx, (void**)&E0, sizeof(zd) * nE)) || (bufs.push_back(E0), 0) ||
-      (s = dev_alloc(ctx, (void**)&E1, sizeof(zd) * nE)) || (bufs.push_back(E1), 0) ||
-      (s = dev_alloc(ctx, (void**)&Y, sizeof(zd) * nY)) || (bufs.push_back(Y), 0) ||
-      (s = dev_alloc(ctx, (void**)&Z, sizeof(zd) * nZ)) || (bufs.push_back(Z), 0)) {
-    cleanup();
-    return s;
-  }
+  qlb_status s;
   {
-    std::vector<zd> h((size_t)d[0] * d[0], mk<double>(0, 0));
-    for (int m = 0; m < d[0]; m++) h[(size_t)m * d[0] + m] = mk<double>(1, 0);
-    QLB_CUDA_TRY(cudaMemcpyAsync(E0, h.data(), sizeof(zd) * h.size(), cudaMemcpyHostToDevice, st->stream));
-    QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
+    size_t a = st->noE, b = st->noE;
+    if ((s = realloc_buf(ctx, &st->oE0, &a, nE)) || (s = realloc_buf(ctx, &st->oE1, &b, nE))) return s;
+    st->noE = std::max(st->noE, nE);
   }
+  if ((s = realloc_buf(ctx, &st->oY, &st->noY, nY)) || (s = realloc_buf(ctx, &st->oZ, &st->noZ, nZ))) return s;
+  zd *E0 = st->oE0, *E1 = st->oE1, *Y = st->oY, *Z = st->oZ;
+  k_transfer_start<<<nblk((long)cap(0) * cap(0)), 256, 0, st->stream>>>(E0, st->d_dims, (long)nE);
+  QLB_CUDA_TRY(cudaGetLastError());
   for (int i = 0; i < L; i++) {
-    int l = d[i], r = d[i + 1], Dl = Wb.D[i], Dr = Wb.D[i + 1];
+    const int Dl = D[i], Dr = D[i + 1];
     GemmDesc g = gdesc();
     g.A = E0;
     g.B = st->site[i];
     g.C = Y;
     g.m = dconst(Dl);
-    g.n = dconst(2 * r);
-    g.k = dconst(l);
+    g.n = dvar(SB(i + 1), 2);
+    g.k = dvar(SB(i));
     g.opA = OP_T;
     g.lda = dconst(Dl);
-    g.ldb = dconst(2 * r);
-    g.ldc = dconst(2 * r);
-    g.sA1 = dconst(l * Dl);
-    g.sC1 = dconst(Dl * 2 * r);
-    g.nb1 = dconst(l);
+    g.ldb = dvar(SB(i + 1), 2);
+    g.ldc = dvar(SB(i + 1), 2);
+    g.sA1 = dvar(SB(i), Dl);
+    g.sC1 = dvar(SB(i + 1), 2 * Dl);
+    g.nb1 = dvar(SB(i));
     g.m_max = Dl;
-    g.n_max = 2 * r;
-    g.nb_max = l;
-    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, st->stream, nullptr));
+    g.n_max = 2 * (int)cap(i + 1);
+    g.nb_max = (int)cap(i);
+    QLB_CUDA_TRY(launch_gemm<double>(g, st->d_dims, st->stream, nullptr));
     g = gdesc();
     g.A = Y;
     g.B = W[i];
     g.C = Z;
-    g.m = dconst(r);
+    g.m = dvar(SB(i + 1));
     g.n = dconst(Dr);
     g.k = dconst(2 * Dl);
     g.opA = OP_T;
-    g.lda = dconst(r);
+    g.lda = dvar(SB(i + 1));
     g.ldb = dconst(Dr);
     g.ldc = dconst(Dr);
-    g.sA1 = dconst(2 * Dl * r);
+    g.sA1 = dvar(SB(i + 1), 2 * Dl);
     g.sB2 = dconst(Dl * 2 * Dr);
-    g.sC1 = dconst(2 * r * Dr);
-    g.sC2 = dconst(r * Dr);
-    g.nb1 = dconst(l);
+    g.sC1 = dvar(SB(i + 1), 2 * Dr);
+    g.sC2 = dvar(SB(i + 1), Dr);
+    g.nb1 = dvar(SB(i));
     g.nb2 = dconst(2);
-    g.m_max = r;
+    g.m_max = (int)cap(i + 1);
     g.n_max = Dr;
-    g.nb_max = 2 * l;
-    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, st->stream, nullptr));
+    g.nb_max = 2 * (int)cap(i);
+    QLB_CUDA_TRY(launch_gemm<double>(g, st->d_dims, st->stream, nullptr));
     g = gdesc();
     g.A = st->site[i];
     g.B = Z;
     g.C = E1;
-    g.m = dconst(r);
-    g.n = dconst(r * Dr);
-    g.k = dconst(2 * l);
+    g.m = dvar(SB(i + 1));
+    g.n = dvar(SB(i + 1), Dr);
+    g.k = dvar(SB(i), 2);
     g.opA = OP_C;
-    g.lda = dconst(r);
-    g.ldb = dconst(r * Dr);
-    g.ldc = dconst(r * Dr);
-    g.m_max = r;
-    g.n_max = r * Dr;
-    QLB_CUDA_TRY(launch_gemm<double>(g, nullptr, st->stream, nullptr));
+    g.lda = dvar(SB(i + 1));
+    g.ldb = dvar(SB(i + 1), Dr);
+    g.ldc = dvar(SB(i + 1), Dr);
+    g.m_max = (int)cap(i + 1);
+    g.n_max = (int)cap(i + 1) * Dr;
+    QLB_CUDA_TRY(launch_gemm<double>(g, st->d_dims, st->stream, nullptr));
     std::swap(E0, E1);
   }
   zd res;
   QLB_CUDA_TRY(cudaMemcpyAsync(&res, E0, sizeof(zd), cudaMemcpyDeviceToHost, st->stream));
   QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
-  cleanup();
   out[0] = res.re;
   out[1] = res.im;
   return QLB_OK;

@@ -26,7 +26,9 @@ qlb_status run_steps(qlb_state* st, int64_t n, bool sync);
 qlb_status read_dims(qlb_state* st, std::vector<int>& d);
 // Branch k of the current Kraus MPO as a builder-layout MPO (left boundary 1).
 qlb_status kraus_branch(qlb_state* st, int k, Mpo& out);
-// Tr(O rho) with an MPO in builder layout (left boundary 1).
-qlb_status expectation_mpo(qlb_state* st, const Mpo& W, double* out);
+// Builder-layout MPO -> step-layout cores in new device buffers (launched on sm).
+qlb_status mpo_step_layout(qlb_ctx* ctx, const Mpo& W, std::vector<zd*>& out, cudaStream_t sm);
+// Tr(O rho) with an MPO in step layout (left boundary 1, bonds D[0..L]).
+qlb_status expectation_mpo(qlb_state* st, const std::vector<zd*>& W, const std::vector<int>& D, double* out);
 
 }  // namespace qlb

@@ -59,6 +59,9 @@ _SIGS = {
     "qlb_state_stream": (_st, [_vp, C.POINTER(_vp)]),
     "qlb_state_poll": (_st, [_vp]),
     "qlb_ctx_memory": (_st, [_vp, C.POINTER(C.c_size_t)]),
+    "qlb_ctx_alloc_count": (_st, [_vp, C.POINTER(C.c_int64)]),
+    "qlb_profile_solver_stats": (_st, [_vp, C.POINTER(C.c_double)]),
+    "qlb_measure_peak": (_st, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "qlb_system_create": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "qlb_system_destroy": (None, [_vp]),
     "qlb_op_build": (_st, [_vp, C.POINTER(qlb_term), C.c_int, C.c_double, C.c_int, C.POINTER(_vp)]),
@@ -150,6 +153,16 @@ class Ctx:
         _check(self.lib.qlb_ctx_memory(self.h, C.byref(b)))
         return b.value
 
+    def alloc_count(self) -> int:
+        n = C.c_int64()
+        _check(self.lib.qlb_ctx_alloc_count(self.h, C.byref(n)))
+        return n.value
+
+    def solver_stats(self):
+        out = (C.c_double * 5)()
+        _check(self.lib.qlb_profile_solver_stats(self.h, out))
+        return dict(solves=out[0], sweeps=out[1], sum_n=out[2], sum_k=out[3], at_limit=out[4])
+
     def profile_enable(self, on=True):
         _check(self.lib.qlb_profile_enable(self.h, int(on)))
 
@@ -175,6 +188,13 @@ class Ctx:
 
 def qlb_create(**opts) -> Ctx:
     return Ctx(**opts)
+
+
+def qlb_measure_peak(device: int, kind: int) -> float:
+    """Measured FMA throughput in TFLOP/s (kind 0: FP64, 1: FP32)."""
+    out = C.c_double()
+    _check(load().qlb_measure_peak(int(device), int(kind), C.byref(out)))
+    return out.value
 
 
 # ---------------------------------------------------------------- systems and operators
