@@ -186,6 +186,8 @@ def run_gpu(args):
     status = st.step(dt, args.warmup)
     ctx.synchronize()
     bonds_before = st.bond_dims()
+    snapshot = st.export()  # the profiled pass below replays exactly these steps
+    ctx.profile_reset()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
         dist.barrier()
@@ -205,25 +207,40 @@ def run_gpu(args):
     ms = [a.elapsed_time(bb) for a, bb in evs]
     value, total_ms = replica_throughput(float(sum(ms)), args.steps, device=f"cuda:{dev}")
     bonds_after = st.bond_dims()
+    solver = ctx.solver_stats()  # counters of the timed (graph-launched) steps
 
-    # kernel-class breakdown of the same steps (events around every launch)
+    # kernel-class breakdown of the same steps: the state is put back to the
+    # snapshot taken before the timed window and the same K steps run again with
+    # CUDA events around every launch (no graph)
+    st.import_(snapshot)
     ctx.profile_enable(True)
     ctx.profile_reset()
     st.step(dt, args.steps)
     ctx.synchronize()
     prof = {qlb.K_NAMES[k]: ctx.profile_read(k) for k in range(qlb.K_COUNT)}
     ctx.profile_enable(False)
+    replay_bonds = st.bond_dims()
     launches_per_step = sum(p["launches"] for p in prof.values()) / args.steps
     dom = max(prof, key=lambda k: prof[k]["ms"])
     dp = prof[dom]
-    peaks = _peaks()
-    fp64_peak = args.fp64_peak_tflops
+    fp64_peak = qlb.qlb_measure_peak(dev, 0)
+    fp32_peak = qlb.qlb_measure_peak(dev, 1)
+    # the FP64 form runs the truncation solves on the FP64 pipe; the mixed form runs
+    # them in double-float on the FP32 pipe (its flops are counted in FP64 terms)
+    peak = fp64_peak if args.precision == 0 or dom != "eig" else fp32_peak
     achieved = dp["flops"] / (dp["ms"] / 1e3) / 1e12 if dp["ms"] > 0 else 0.0
-    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
-                "peak_source": "FP64 nominal 1.25 TFLOP/s (recipe table; no FP64 figure in the measured peaks)",
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": ("measured FP64 FMA throughput of this GPU (qlb_measure_peak)"
+                                if peak == fp64_peak else "measured FP32 FMA throughput of this GPU"),
                 "launches": dp["launches"], "ms_per_launch": dp["ms"] / max(1, dp["launches"]),
-                "flops_per_launch": dp["flops"] / max(1, dp["launches"])}
+                "flops_per_launch": dp["flops"] / max(1, dp["launches"]),
+                "class_ms_per_step": dp["ms"] / args.steps, "step_ms": total_ms / args.steps,
+                "same_steps_as_timed": replay_bonds == bonds_after}
+    nsol = max(1.0, solver["solves"])
+    solver_line = {"solves_per_step": solver["solves"] / args.steps, "sweeps_per_solve": solver["sweeps"] / nsol,
+                   "mean_n": solver["sum_n"] / nsol, "mean_kept": solver["sum_k"] / nsol,
+                   "at_limit": solver["at_limit"]}
 
     # end to end through the public API: host mode vector in (init), K steps each
     # followed by a read-back of the photon number; the system's operators and
@@ -253,6 +270,8 @@ def run_gpu(args):
                    "bonds_after": bonds_after, "step_status": int(status)},
         "roofline": roofline,
         "kernel_classes_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+        "solver": solver_line,
+        "peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak, "source": "qlb_measure_peak, this run"},
         "e2e": {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps, "observables": [n_obs.real, p_obs.real]},
         "gpu_launches": int(round(launches_per_step * args.steps)),
@@ -297,7 +316,6 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", type=int, default=0)
-    ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--serving-step-scale", type=float, default=0.005)

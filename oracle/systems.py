@@ -1,9 +1,11 @@
 """Dense oracle versions of the paper's model systems (test infrastructure only).
 
-Built from the same parameter sets as the product path (paper_2605_27515_gb300.
-inputs) but with the oracle's own dense operators, so the two sides share only
-the parameters.  See paper_2605_27515_gb300/systems.py for the formulas; the
-mode orders are the same (cat_pair: [b1, a1, a2, b2]).
+Each builder takes a raw parameter set (the dicts of the shared input module:
+mode sizes, rates, time step) and derives everything else itself from the
+paper's formulas: the Z-gate operating point (Sec. VI), the initial cat and
+transmon states, the resonator drive schedule (Sec. VII).  Nothing here imports
+the product package.  Mode orders: cat_pair is [b1, a1, a2, b2], transmon and
+transmon_eig are [transmon, resonator], z_gate is [memory a, buffer b].
 """
 from __future__ import annotations
 
@@ -43,7 +45,35 @@ def cat(cfg):
     return DenseSystem(dims, H, Ls, observables=obs, init=[D.fock(N, 0)])
 
 
-def transmon(cfg, nsteps, f_table, init):
+def transmon_charge_hamiltonian(Nt, ec, ej, ng=0.0):
+    """H_t = 4 E_C (n_t - n_g)^2 - E_J cos(phi_t) in the charge basis (Sec. VII, Eq.
+    transmon), charges j - Nt/2 for j = 0..Nt-1, cos(phi) cut open at both ends."""
+    nt = D.op_charge(Nt, Nt // 2) - ng * np.eye(Nt)
+    return 4.0 * ec * nt @ nt - ej * D.op_cos_phi(Nt)
+
+
+def transmon_ground(Nt, ec, ej, ng=0.0):
+    """Lowest eigenvector of the charge-basis transmon (the start of Sec. VII's run)."""
+    w, v = np.linalg.eigh(transmon_charge_hamiltonian(Nt, ec, ej, ng))
+    return v[:, 0].astype(np.complex128)
+
+
+def drive_table(cfg, nsteps, t0=0.0):
+    """Resonator drive f(t_n) = eps(t_n) cos(w_r t_n) at the left ends t_n = t0 + n h,
+    eps ramped linearly to eps_max = (eps/kappa) kappa over ramp/kappa (reading of
+    Sec. VII, whose drive frequency and ramp the text leaves open)."""
+    t = t0 + cfg["dt"] * np.arange(nsteps)
+    eps_max = cfg["eps_over_kappa"] * cfg["kappa"]
+    return eps_max * np.minimum(1.0, t * cfg["kappa"] / cfg["ramp_kappa_t"]) * np.cos(cfg["wr"] * t)
+
+
+def transmon(cfg, nsteps, f_table=None, init=None):
+    """Transmon (charge basis) x resonator (Sec. VII): H0 = 4 E_C (n_t - n_g)^2
+    - E_J cos(phi_t) + w_r a^dag a + g n_t (a + a^dag), H1 = a + a^dag with f(t_n),
+    L = sqrt(kappa) a.  The coupling g n_t (a + a^dag) is the paper's
+    -i g n_t (a - a^dag) after a -> -i a (a diagonal phase change of the resonator
+    basis, which leaves every observable used here unchanged).  Start: the
+    transmon ground state x resonator vacuum."""
     Rt, Rr = cfg["R"]
     Nt, Nr = 2 ** Rt, 2 ** Rr
     off = Nt // 2
@@ -51,14 +81,18 @@ def transmon(cfg, nsteps, f_table, init):
     ec = cfg["ec"]
     ej = cfg["ej_over_ec"] * ec
     g = cfg["g_over_ec"] * ec
-    nt = D.op_charge(Nt, off) - cfg.get("ng", 0.0) * np.eye(Nt)
     ntc = D.op_charge(Nt, off)
     a, ad = D.op_a(Nr), D.op_adag(Nr)
-    H0 = D.Operator(dims, [(4 * ec, {0: nt @ nt}), (-ej, {0: D.op_cos_phi(Nt)}), (cfg["wr"], {1: D.op_num(Nr)}),
-                           (g, {0: ntc, 1: a}), (g, {0: ntc, 1: ad})])
+    Ht = transmon_charge_hamiltonian(Nt, ec, ej, cfg.get("ng", 0.0))
+    H0 = D.Operator(dims, [(1.0, {0: Ht}), (cfg["wr"], {1: D.op_num(Nr)}), (g, {0: ntc, 1: a}),
+                           (g, {0: ntc, 1: ad})])
     H1 = D.Operator(dims, [(1.0, {1: a}), (1.0, {1: ad})])
     Ls = [D.Operator.local(dims, 1, a, np.sqrt(cfg["kappa"]))]
     obs = {"n_c": D.Operator.local(dims, 1, D.op_num(Nr)), "n_t2": D.Operator.local(dims, 0, ntc @ ntc)}
+    if f_table is None:
+        f_table = drive_table(cfg, nsteps)
+    if init is None:
+        init = [transmon_ground(Nt, ec, ej, cfg.get("ng", 0.0)), D.fock(Nr, 0)]
     return DenseSystem(dims, H0, Ls, H1=H1, f_table=f_table, observables=obs, init=init)
 
 
@@ -133,7 +167,7 @@ def transmon_eigenbasis(ec, ej, K, n_cut=500, tie=1e-9):
     return E, nt, Psi
 
 
-def transmon_eig(cfg, nsteps, f_table):
+def transmon_eig(cfg, nsteps, f_table=None):
     """Transmon x resonator with the transmon in its eigenbasis (Sec. VII,
     numerical experiment): H0 = diag(eps_alpha - eps_0) + w_r a^dag a
     + g n_t (a + a^dag), drive f(t_n) (a + a^dag), L = sqrt(kappa) a; observables
@@ -154,20 +188,41 @@ def transmon_eig(cfg, nsteps, f_table):
     H1 = D.Operator(dims, [(1.0, {1: a}), (1.0, {1: ad})])
     Ls = [D.Operator.local(dims, 1, a, np.sqrt(cfg["kappa"]))]
     obs = {"n_c": D.Operator.local(dims, 1, D.op_num(Nr)), "n_t": D.Operator.local(dims, 0, D.op_num(K))}
+    if f_table is None:
+        f_table = drive_table(cfg, nsteps)
     return DenseSystem(dims, H0, Ls, H1=H1, f_table=f_table, observables=obs, init=[D.fock(K, 0), D.fock(Nr, 0)])
 
 
-def z_gate(cfg, init):
+def z_gate_params(cfg):
+    """The Z-gate operating point of Sec. VI's numerical experiment, from the raw
+    parameters (R_a, g2, kappa_b, theta): |alpha|^2 = N_a / 3 (unless given);
+    the buffer is dark for g2 a^2 + eps_d = 0 on the cat, so eps_d = -g2 alpha^2
+    (reading of alpha = -sqrt(eps_d / g2), Sec. VI, with H_stab as written);
+    eps_Z = (1/10) 4 g2^2 / kappa_b; the gate time from theta = 4 alpha T_Z eps_Z."""
+    Na = 2 ** cfg["R"][0]
+    alpha2 = cfg.get("alpha2", Na / 3.0)
+    alpha = float(np.sqrt(alpha2))
+    eps_z = 4.0 * cfg["g2"] ** 2 / cfg["kb"] / 10.0
+    t_z = cfg["theta"] / (4.0 * alpha * eps_z)
+    return dict(alpha2=alpha2, alpha=alpha, eps_d=-cfg["g2"] * alpha2, eps_z=eps_z, t_z=t_z,
+                steps=int(round(t_z / cfg["dt"])))
+
+
+def cat_state(N, alpha, parity=+1):
+    """Normalised cat |alpha> + parity |-alpha> from the truncated coherent states."""
+    v = D.coherent(N, alpha) + parity * D.coherent(N, -alpha)
+    return v / np.linalg.norm(v)
+
+
+def z_gate(cfg, init=None):
     """Z gate on a cat qubit with its buffer (Sec. VI, Eq. cb and Eq. Hz), modes
     [a, b]: H = g2 (a^dag^2 b + a^2 b^dag) + eps_d (b + b^dag) + eps_Z (a + a^dag),
-    L_b = sqrt(kappa_b) b (+ sqrt(kappa_a) a).  Parameters from the product's
-    parameter set; `init` is the pair of mode vectors."""
-    from paper_2605_27515_gb300 import inputs
-
+    L_b = sqrt(kappa_b) b (+ sqrt(kappa_a) a).  Start (unless `init` is given): the
+    even cat of amplitude alpha x buffer vacuum."""
     Ra, Rb = cfg["R"]
     Na, Nb = 2 ** Ra, 2 ** Rb
     dims = (Na, Nb)
-    zp = inputs.z_gate_params(cfg)
+    zp = z_gate_params(cfg)
     g2 = cfg["g2"]
     A, Ad, B, Bd = D.op_a(Na), D.op_adag(Na), D.op_a(Nb), D.op_adag(Nb)
     H = D.Operator(dims, [(g2, {0: Ad @ Ad, 1: B}), (g2, {0: A @ A, 1: Bd}), (zp["eps_d"], {1: B}),
@@ -177,5 +232,6 @@ def z_gate(cfg, init):
         Ls.append(D.Operator.local(dims, 0, A, np.sqrt(cfg["ka"])))
     obs = {"parity_a": D.Operator.local(dims, 0, D.op_parity(Na)), "n_a": D.Operator.local(dims, 0, D.op_num(Na)),
            "n_b": D.Operator.local(dims, 1, D.op_num(Nb))}
+    if init is None:
+        init = [cat_state(Na, zp["alpha"], +1), D.fock(Nb, 0)]
     return DenseSystem(dims, H, Ls, observables=obs, init=init)
-

@@ -3,7 +3,8 @@
 This module holds parameters and random numbers only, none of the method's
 arithmetic: it names the physical systems (mode sizes, rates, drive, time step,
 truncation settings) and draws the seeded random inputs (request mixes, random
-initial vectors).  Each side builds its own operators from these parameters.
+initial vectors).  Each side builds its own operators, derived operating points
+and initial states from these parameters.
 
 Systems (all from the paper's applications, Sec. VI and Sec. VII):
   cat_r5        single cat mode, N = 32: L1 = sqrt(k2)(a^2 - alpha^2),
@@ -17,10 +18,10 @@ Systems (all from the paper's applications, Sec. VI and Sec. VII):
                 eps(t) cos(w_r t)(a + a^dag), L = sqrt(kappa) a.
   transmon_eig  the same transmon x resonator with the transmon in its
                 eigenbasis (|n| <= 500 charges diagonalised, lowest 2^5 states).
-  z_gate        memory cat (N_a = 2^R_a, alpha^2 = N_a / 3) with a lossy buffer
-                (N_b = 16), g2 = 1, kappa_b = 10 g2, eps_Z = 4 g2^2 / (10 kappa_b),
-                theta = pi, kappa_a = 0 (Sec. VI numerical experiment), even-cat
-                start, T_Z = theta / (4 alpha eps_Z).
+  z_gate        memory cat (N_a = 2^R_a) with a lossy buffer (N_b = 16),
+                g2 = 1, kappa_b = 10 g2, theta = pi, kappa_a = 0 (Sec. VI numerical
+                experiment); the operating point (alpha, eps_d, eps_Z, T_Z) and the
+                even-cat start are derived by each side from these.
   cat_pair      two storage cats (N = 256) each with a buffer (N = 16),
                 three-wave mixing g2 (a^2 b^dag + h.c.), buffer drive, beam
                 splitter J (a1^dag a2 + h.c.), 16 variants of J.
@@ -119,40 +120,3 @@ def random_vector(n: int, seed: int) -> np.ndarray:
     """Seeded complex Gaussian vector (not normalised)."""
     rng = np.random.default_rng(seed)
     return rng.normal(size=n) + 1j * rng.normal(size=n)
-
-
-def transmon_ground_charge(Nt: int, offset: int, ec: float, ej: float, ng: float = 0.0) -> np.ndarray:
-    """Initial transmon vector of the transmon system: the lowest eigenvector of
-    4 Ec (n - ng)^2 - Ej cos(phi) on the charge states n = j - offset (Sec. VII,
-    Eq. transmon), cut open at both ends."""
-    n = np.arange(Nt) - offset
-    H = np.diag(4 * ec * (n - ng) ** 2).astype(np.complex128)
-    for j in range(Nt - 1):
-        H[j, j + 1] = H[j + 1, j] = -ej / 2
-    w, v = np.linalg.eigh(H)
-    return v[:, 0]
-
-
-def z_gate_params(cfg: dict) -> dict:
-    """Derived Z-gate parameters (Sec. VI): alpha^2 = N_a / 3, eps_d = -g2 alpha^2,
-    eps_Z = 4 g2^2 / (10 kappa_b), T_Z = theta / (4 alpha eps_Z), steps = T_Z / dt."""
-    Na = 2 ** cfg["R"][0]
-    alpha2 = cfg.get("alpha2", Na / 3.0)
-    alpha = float(np.sqrt(alpha2))
-    eps_z = 0.1 * 4.0 * cfg["g2"] ** 2 / cfg["kb"]
-    tz = cfg["theta"] / (4.0 * alpha * eps_z)
-    return dict(alpha2=alpha2, alpha=alpha, eps_d=-cfg["g2"] * alpha2, eps_z=eps_z, t_z=tz,
-                steps=int(round(tz / cfg["dt"])))
-
-
-def cat_vector(N: int, alpha: float, parity: int = +1) -> np.ndarray:
-    """Normalised cat |alpha> + parity |-alpha> in an N-level Fock space, from the
-    coherent amplitudes alpha^n / sqrt(n!) (each coherent part truncated)."""
-    c = np.zeros(N, dtype=np.complex128)
-    c[0] = 1.0
-    for n in range(1, N):
-        c[n] = c[n - 1] * alpha / np.sqrt(n)
-    sign = (-1.0) ** np.arange(N)
-    v = c + parity * sign * c
-    return v / np.linalg.norm(v)
-

@@ -22,6 +22,42 @@ from . import inputs
 from . import qlb as Q
 
 
+def transmon_ground_charge(Nt: int, offset: int, ec: float, ej: float, ng: float = 0.0) -> np.ndarray:
+    """Initial transmon vector of the transmon system (input preparation for the
+    C-ABI): the lowest eigenvector of 4 Ec (n - ng)^2 - Ej cos(phi) on the charge
+    states n = j - offset (Sec. VII, Eq. transmon), cut open at both ends."""
+    n = np.arange(Nt) - offset
+    H = np.diag(4 * ec * (n - ng) ** 2).astype(np.complex128)
+    for j in range(Nt - 1):
+        H[j, j + 1] = H[j + 1, j] = -ej / 2
+    w, v = np.linalg.eigh(H)
+    return v[:, 0]
+
+
+def z_gate_params(cfg: dict) -> dict:
+    """Derived Z-gate parameters (Sec. VI): alpha^2 = N_a / 3, eps_d = -g2 alpha^2,
+    eps_Z = 4 g2^2 / (10 kappa_b), T_Z = theta / (4 alpha eps_Z), steps = T_Z / dt."""
+    Na = 2 ** cfg["R"][0]
+    alpha2 = cfg.get("alpha2", Na / 3.0)
+    alpha = float(np.sqrt(alpha2))
+    eps_z = 0.1 * 4.0 * cfg["g2"] ** 2 / cfg["kb"]
+    tz = cfg["theta"] / (4.0 * alpha * eps_z)
+    return dict(alpha2=alpha2, alpha=alpha, eps_d=-cfg["g2"] * alpha2, eps_z=eps_z, t_z=tz,
+                steps=int(round(tz / cfg["dt"])))
+
+
+def cat_vector(N: int, alpha: float, parity: int = +1) -> np.ndarray:
+    """Normalised cat |alpha> + parity |-alpha> in an N-level Fock space, from the
+    coherent amplitudes alpha^n / sqrt(n!) (each coherent part truncated)."""
+    c = np.zeros(N, dtype=np.complex128)
+    c[0] = 1.0
+    for n in range(1, N):
+        c[n] = c[n - 1] * alpha / np.sqrt(n)
+    sign = (-1.0) ** np.arange(N)
+    v = c + parity * sign * c
+    return v / np.linalg.norm(v)
+
+
 def vacuum(N):
     v = np.zeros(N, dtype=np.complex128)
     v[0] = 1.0
@@ -78,7 +114,7 @@ def build_transmon(ctx, cfg, nsteps=None):
     ops["L"] = s.op([(np.sqrt(cfg["kappa"]), [(1, Q.F_A)])])
     s.add_jump(ops["L"])
     obs = {"n_c": s.op([(1.0, [(1, Q.F_NUM)])]), "n_t2": s.op([(1.0, [(0, Q.F_CHARGE, 2, float(off))])])}
-    init = [inputs.transmon_ground_charge(Nt, off, ec, ej, cfg.get("ng", 0.0)), vacuum(2 ** Rr)]
+    init = [transmon_ground_charge(Nt, off, ec, ej, cfg.get("ng", 0.0)), vacuum(2 ** Rr)]
     return Built(s, ops, init, obs, cfg, f)
 
 
@@ -170,7 +206,7 @@ def build_z_gate(ctx, cfg):
     start in the even cat x buffer vacuum.  Observables: memory parity, photon
     numbers."""
     Ra, Rb = cfg["R"]
-    zp = inputs.z_gate_params(cfg)
+    zp = z_gate_params(cfg)
     g2 = cfg["g2"]
     s = Q.System(ctx, [Ra, Rb])
     a, b = 0, 1
@@ -187,7 +223,7 @@ def build_z_gate(ctx, cfg):
         s.add_jump(ops["La"])
     obs = {"parity_a": s.op([(1.0, [(a, Q.F_PARITY)])]), "n_a": s.op([(1.0, [(a, Q.F_NUM)])]),
            "n_b": s.op([(1.0, [(b, Q.F_NUM)])])}
-    init = [inputs.cat_vector(2 ** Ra, zp["alpha"], +1), vacuum(2 ** Rb)]
+    init = [cat_vector(2 ** Ra, zp["alpha"], +1), vacuum(2 ** Rb)]
     return Built(s, ops, init, obs, cfg)
 
 

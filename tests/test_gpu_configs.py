@@ -70,10 +70,7 @@ def test_transmon_check_size():
     cfg["dt"] = dt
     c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])
     b = systems.build(c, cfg, nsteps=nsteps)
-    Nt = 2 ** cfg["R"][0]
-    init = [inputs.transmon_ground_charge(Nt, Nt // 2, cfg["ec"], cfg["ej_over_ec"] * cfg["ec"]),
-            D.fock(2 ** cfg["R"][1], 0)]
-    ds = OS.transmon(cfg, nsteps, b.f_table, init)
+    ds = OS.transmon(cfg, nsteps)  # the oracle's own drive table and ground state
     worst = _compare(b, ds, dt, nsteps, 5, ["n_c", "n_t2"])
     assert max(worst.values()) < 1e-6, worst
     c.close()
@@ -89,7 +86,7 @@ def test_transmon_eigenbasis_check_size():
     cfg["dt"] = dt
     c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])
     b = systems.build(c, cfg, nsteps=nsteps)
-    ds = OS.transmon_eig(cfg, nsteps, b.f_table)
+    ds = OS.transmon_eig(cfg, nsteps)
     worst = _compare(b, ds, dt, nsteps, 5, ["n_c", "n_t"])
     assert max(worst.values()) < 1e-6, worst
     c.close()

@@ -37,7 +37,7 @@ def test_z_gate_check_size():
     cfg["chi_mu_max"] = 32
     c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])
     b = systems.build(c, cfg)
-    ds = OS.z_gate(cfg, b.init)
+    ds = OS.z_gate(cfg)
     worst = _compare(b, ds, cfg["dt"], 600, 100, ["parity_a", "n_a", "n_b"])
     assert max(worst.values()) < 1e-6, worst
     c.close()
