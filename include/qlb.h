@@ -79,7 +79,8 @@ typedef struct {
                             frame that is not orthonormal, so it must cut far below tol) */
   double degeneracy_gap; /* singular values within this relative gap are one cluster and
                             are never split by a cut (default 1e-10) */
-  int max_sweeps;        /* Jacobi sweep limit before QLB_ENOTCONV (default 40) */
+  int max_sweeps;        /* Jacobi sweep limit before QLB_ENOTCONV (default 40); below 60
+                            it also caps the QL iterations per eigenvalue */
   size_t hbm_budget;     /* bytes of device memory the context may hold; 0 = no limit */
   int stream_ordered;    /* 1: qlb_step only enqueues; 0 (default): it synchronises */
 } qlb_options;
@@ -268,11 +269,13 @@ qlb_status qlb_profile_read(qlb_ctx* ctx, int kclass, double* ms, int64_t* launc
                             double* bytes);
 qlb_status qlb_profile_reset(qlb_ctx* ctx);
 /* Eigen-solver counters of the context since the last qlb_profile_reset, kept
- * whether or not profiling is on (also inside captured step graphs):
- * out5[0] solves, out5[1] Jacobi sweeps plus QL passes, out5[2] sum of the
- * runtime matrix sizes n, out5[3] sum of the kept counts k, out5[4] solves that
- * reached the sweep (or QL iteration) limit.  Synchronises the device. */
-qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out5);
+ * whether or not profiling is on (also inside captured step graphs); the first
+ * min(n_out, 7) of: out[0] solves, out[1] Jacobi sweeps plus QL passes, out[2] sum
+ * of the runtime matrix sizes n, out[3] sum of the kept counts k, out[4] solves
+ * that reached the sweep (or QL iteration) limit, out[5] solves whose matrices did
+ * not fit in shared memory (global-memory workspace), out[6] the largest runtime
+ * size n.  Synchronises the device. */
+qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out, int n_out);
 
 /* Measured fused multiply-add throughput of device `device` in TFLOP/s:
  * kind 0 = FP64, kind 1 = FP32 (independent FMA chains over every SM, timed with

@@ -921,11 +921,11 @@ QLB_API qlb_status qlb_profile_reset(qlb_ctx* ctx) {
   return QLB_OK;
 }
 
-QLB_API qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out5) {
-  CHECK_ARG(ctx && out5, "null argument");
+QLB_API qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out, int n_out) {
+  CHECK_ARG(ctx && out && n_out >= 0, "null argument");
   QLB_CUDA_TRY(cudaDeviceSynchronize());
   double h[8] = {0};
   if (ctx->d_solver) QLB_CUDA_TRY(cudaMemcpy(h, ctx->d_solver, sizeof(h), cudaMemcpyDeviceToHost));
-  for (int i = 0; i < 5; i++) out5[i] = h[i];
+  for (int i = 0; i < n_out && i < 7; i++) out[i] = h[i];
   return QLB_OK;
 }

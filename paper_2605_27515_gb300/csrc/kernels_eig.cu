@@ -7,15 +7,13 @@
 // and (c, s) the real symmetric Schur pair of [[G_pp, |G_pq|], [|G_pq|, G_qq]]
 // (Golub & Van Loan, sym.schur2); G <- J^dag G J, V <- V J.  A pair is skipped
 // when |G_pq| <= n eps sqrt(|G_pp G_qq|) (the relative criterion that keeps small
-// eigenvalues of a Gram matrix accurate), below an absolute floor of eps Tr G / 10
-// (under the rounding already carried by the Gram matrix itself), or when both
-// G_pp and G_qq are at most n eps Tr G: two directions that are both numerically
-// zero hold nothing a rotation between them could resolve, and rotating them only
-// trades rounding noise back and forth until the sweep limit.  Pairs of a real
-// direction with a numerically zero one are still rotated, so real weight is
-// never mixed into a direction the truncation may drop.  A sweep with no rotation
-// ends the solve.  At the sweep limit the solve is accepted when the off-diagonal
-// norm left is below n eps Tr G.
+// eigenvalues of a Gram matrix accurate) or below an absolute floor of
+// eps Tr G / 10, under the rounding already carried by the Gram matrix itself.
+// (A looser floor for pairs of tiny diagonals was tried and dropped: directions of
+// relative weight ~1e-15 are real content that the untruncated form must keep to
+// reach 1e-10 in the observables.)  A sweep with no rotation ends the solve.  At
+// the sweep limit the solve is accepted when the off-diagonal norm left is below
+// n eps Tr G.
 //
 // Each round has three barriers: rotation parameters, row update (J^dag G), and
 // column update (G J, V J) which also writes the annihilated entries as exact
@@ -136,6 +134,8 @@ __device__ void eig_finish(const EigDesc& e, int* d, int n, const double* lam, c
       atomicAdd(e.solver_stats + 0, 1.0);
       atomicAdd(e.solver_stats + 2, (double)n);
       atomicAdd(e.solver_stats + 3, (double)k);
+      // largest runtime size: non-negative doubles order like their bit patterns
+      atomicMax((unsigned long long*)(e.solver_stats + 6), (unsigned long long)__double_as_longlong((double)n));
     }
     if (e.err) {
       if (unconverged) atomicOr(e.err, 1);
@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
   }
   const int np = n + (n & 1);
   const bool use_smem = 2L * np * np * (long)sizeof(cx<R>) <= (long)dyn_bytes;
+  if (!use_smem && e.solver_stats && tid == 0) atomicAdd(e.solver_stats + 5, 1.0);
   cx<R>* Gs = use_smem ? (cx<R>*)smem_raw : work;
   cx<R>* Vs = Gs + (long)np * np;
   __shared__ R rc[256];
@@ -212,8 +213,6 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
   }
   __syncthreads();
   const R abs_thr = s_thr;
-  // both diagonals at or below this: a pair of numerically zero directions
-  const R zero_floor = to_r<R>(Eps<R>::v * (double)n * s_tr);
   // relative floor: rounding in the row/column updates leaves off-diagonals of
   // order n eps sqrt(G_pp G_qq); asking for less would rotate noise forever
   const R rel_tol = to_r<R>(Eps<R>::v * (double)(n > 8 ? n : 8));
@@ -240,8 +239,7 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
           R a = Gs[(long)p * np + p].re, b = Gs[(long)q * np + q].re;
           cx<R> gpq = Gs[(long)p * np + q];
           R x = sqrt(cabs2(gpq));
-          const bool both_zero = fabs(a) <= zero_floor && fabs(b) <= zero_floor;
-          if (!both_zero && x > rel_tol * sqrt(fabs(a * b)) && x > abs_thr && x > zero) {
+          if (x > rel_tol * sqrt(fabs(a * b)) && x > abs_thr && x > zero) {
             R tau = (b - a) / (x + x);
             R t = fabs(tau) > to_r<R>(1e15) ? to_r<R>(0.5) / tau
                                             : (tau >= zero ? one : -one) / (fabs(tau) + sqrt(one + tau * tau));
@@ -375,6 +373,7 @@ __global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd*
   }
   const int np = n + (n & 1);
   const bool use_smem = 2L * np * np * (long)sizeof(zd) <= (long)dyn_bytes;
+  if (!use_smem && e.solver_stats && tid == 0) atomicAdd(e.solver_stats + 5, 1.0);
   zd* A = use_smem ? (zd*)smem_raw : work;
   zd* Qt = A + (long)np * np;
   __shared__ zd s_v[512], s_p[512], s_u[512];
@@ -509,6 +508,9 @@ __global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd*
   // pass, the other warps apply those of the previous pass to the rows of W.
   zd* Wt = Qt;
   const double floor_abs = 1e-3 * eps * s_tr;
+  // QL iterations allowed per eigenvalue (usually 1-3 are needed); the context's
+  // sweep limit caps it as well, so a forced limit of 1 is observable here too
+  const int it_limit = e.max_sweeps < HEEV_MAX_IT ? (e.max_sweeps > 0 ? e.max_sweeps : 1) : HEEV_MAX_IT;
   int ql_l = 0, ql_it = 0;
   long n_rot = 0;
   for (int t = 0;; t++) {
@@ -528,7 +530,7 @@ __global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd*
           ql_it = 0;
           continue;
         }
-        if (++ql_it > HEEV_MAX_IT) {
+        if (++ql_it > it_limit) {
           s_fail = 1;
           s_e[m - 1] = 0.0;  // give up on this coupling; flagged as unconverged
           continue;

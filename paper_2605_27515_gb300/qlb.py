@@ -60,7 +60,7 @@ _SIGS = {
     "qlb_state_poll": (_st, [_vp]),
     "qlb_ctx_memory": (_st, [_vp, C.POINTER(C.c_size_t)]),
     "qlb_ctx_alloc_count": (_st, [_vp, C.POINTER(C.c_int64)]),
-    "qlb_profile_solver_stats": (_st, [_vp, C.POINTER(C.c_double)]),
+    "qlb_profile_solver_stats": (_st, [_vp, C.POINTER(C.c_double), C.c_int]),
     "qlb_measure_peak": (_st, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
     "qlb_system_create": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "qlb_system_destroy": (None, [_vp]),
@@ -159,9 +159,10 @@ class Ctx:
         return n.value
 
     def solver_stats(self):
-        out = (C.c_double * 5)()
-        _check(self.lib.qlb_profile_solver_stats(self.h, out))
-        return dict(solves=out[0], sweeps=out[1], sum_n=out[2], sum_k=out[3], at_limit=out[4])
+        out = (C.c_double * 7)()
+        _check(self.lib.qlb_profile_solver_stats(self.h, out, 7))
+        return dict(solves=out[0], sweeps=out[1], sum_n=out[2], sum_k=out[3], at_limit=out[4],
+                    global_ws=out[5], max_n=out[6])
 
     def profile_enable(self, on=True):
         _check(self.lib.qlb_profile_enable(self.h, int(on)))

@@ -342,3 +342,47 @@ def test_errors_are_codes(ctx):
         s.op([(1.0, [(0, Q.F_A)])])
     assert e.value.status == Q.ENOMEM
     c.close()
+
+
+# ------------------------------------------------------------------ failure paths
+
+
+def test_sweep_limit_returns_enotconv():
+    """A context whose eigen-solves may take one sweep (one QL iteration per
+    eigenvalue) cannot converge a step's truncation of a random mixed state:
+    qlb_step returns QLB_ENOTCONV with a message, and the context stays usable."""
+    c = Q.Ctx(device=0, tol=1e-28, chi_max=256, chi_mu_max=128, max_sweeps=1)
+    s, H, Ls, Hd, Lds, vecs, O, dims = _random_system(c, [3], seed=23)
+    statuses = []
+    try:
+        st = s.state(vecs)
+        for _ in range(3):
+            try:
+                statuses.append(st.step(0.05, 1))
+            except Q.QlbError as e:
+                statuses.append(e.status)
+                assert "sweep limit" in str(e)
+                break
+        st.close()
+    except Q.QlbError as e:  # the state's first truncation may already stop
+        statuses.append(e.status)
+    assert Q.ENOTCONV in statuses, statuses
+    s.close()
+    c.close()
+    c2 = Q.Ctx(device=0, **EXACT)
+    s2, *_rest, vecs2, _O, _d = _random_system(c2, [3], seed=23)
+    st2 = s2.state(vecs2)
+    assert st2.step(0.05, 2) >= 0
+    st2.close()
+    s2.close()
+    c2.close()
+
+
+def test_nonfinite_host_input_returns_enonfinite(ctx):
+    s = Q.System(ctx, [3])
+    v = D.fock(8, 0).copy()
+    v[3] = np.nan
+    with pytest.raises(Q.QlbError) as e:
+        s.state([v])
+    assert e.value.status == Q.ENONFINITE
+    s.close()

@@ -1,8 +1,11 @@
 """GPU parity of the Z-gate system (Sec. VI): a cat qubit with its lossy buffer
 at (N_a, N_b) = (8, 4), against the dense FP64 oracle within 1e-6 (truncated form).
 Kept in a file of its own, collected after the other GPU parity files."""
+import numpy as np
 import pytest
 
+from oracle import dense as D
+from oracle import mps as MPS
 from oracle import systems as OS
 from paper_2605_27515_gb300 import inputs
 from paper_2605_27515_gb300 import qlb as Q
@@ -40,4 +43,39 @@ def test_z_gate_check_size():
     ds = OS.z_gate(cfg)
     worst = _compare(b, ds, cfg["dt"], 600, 100, ["parity_a", "n_a", "n_b"])
     assert max(worst.values()) < 1e-6, worst
+    c.close()
+
+
+def test_z_gate_config_settings_match_the_oracle_mps_step():
+    """At the configuration's own truncation (tol 1e-8, chi_mu <= 16, chi <= 64),
+    where the purification cap binds at (N_a, N_b) = (8, 4), the device step
+    against the oracle's own purified-MPS step (exact MPO.MPS products, matrix
+    addition, right-to-left SVD truncation, purification truncation) at the same
+    caps and tolerance: memory parity and photon numbers within 1e-9 over 600
+    steps of dt = 1e-3."""
+    cfg = inputs.config("z_gate")
+    cfg.update(cfg.pop("check"))
+    assert cfg["tol"] == 1e-8 and cfg["chi_mu_max"] == 16
+    h = cfg["dt"]
+    c = Q.Ctx(device=0, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])
+    b = systems.build(c, cfg)
+    st = b.sys.state(b.init)
+    ds = OS.z_gate(cfg)
+    Ks = [D.u1(ds.H0, ds.Ls, h).dense()] + [np.sqrt(h) * L.dense() for L in ds.Ls]
+    nbits = sum(cfg["R"])
+    mpos = MPS.kraus_mpos(Ks, nbits)
+    cores = MPS.product_state(ds.init, cfg["R"])
+    obs = {n: ds.observables[n].dense() for n in ("parity_a", "n_a", "n_b")}
+    worst = 0.0
+    for k in range(1, 601):
+        cores, info = MPS.kraus_step(cores, mpos, cfg["tol"], cfg["chi_max"], cfg["chi_mu_max"])
+        st.step(h, 1)
+        if k % 100 == 0:
+            for n, O in obs.items():
+                g = st.expectation(b.observables[n]).real
+                o = MPS.expectation(cores, O).real
+                worst = max(worst, abs(g - o))
+    assert info["chi_mu"] == 16  # the cap binds
+    assert worst < 1e-9, worst
+    st.close()
     c.close()

@@ -3,7 +3,8 @@ single cat mode at N = 512 (alpha^2 = 32, Zeno drive eps_Z = 0.1, dt = 5e-4,
 chi <= 64, chi_mu <= 16, cutoff 1e-12, stream-ordered context), against the dense
 FP64 oracle at N = 512 every 5 steps over the first 30, in both precision forms;
 plus properties that hold at any size (trace, purity, parity range, caps, and the
-explicit scheme's instability warning for this step size).  Kept in a file of its
+explicit scheme's instability warning for this step size), and the solver counters
+showing that the eigen-solves reached size 128 in global memory.  Kept in a file of its
 own, collected after the other GPU parity files."""
 import pytest
 
@@ -29,6 +30,7 @@ def test_full_size_first_steps_match_oracle(oracle_records, precision):
                 chi_mu_max=cfg["chi_mu_max"], stream_ordered=1)
     b = systems.build(ctx, cfg)
     st = b.sys.state(b.init)
+    ctx.profile_reset()
     done = 0
     worst = 0.0
     for step, (n_o, p_o) in oracle_records[1:]:
@@ -44,5 +46,10 @@ def test_full_size_first_steps_match_oracle(oracle_records, precision):
         bd = st.bond_dims()
         assert bd[0] <= cfg["chi_mu_max"] and max(bd[1:]) <= cfg["chi_max"]
     assert worst < 1e-6, worst
+    sv = ctx.solver_stats()
+    # the zip-up bonds reach the cap of 64, so the eigen-solves run at 2 x 64 = 128,
+    # past the shared-memory sizes (the global-memory workspace path)
+    assert sv["max_n"] >= 128, sv
+    assert sv["global_ws"] >= 1, sv
     st.close()
     ctx.close()
