@@ -24,6 +24,8 @@
 // (the mixed form): the same rotations on the FP32 pipes with ~48-bit significands.
 // Input G and the output vectors are FP64 in both cases.
 
+#include <cooperative_groups.h>
+
 #include <type_traits>
 
 #include "df64.cuh"
@@ -332,6 +334,277 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
   eig_finish<R, NT>(e, d, n, s_lam, Vs, np, 1, unconverged, s_perm, s_w, &s_k, &s_bad);
 }
 
+// The same cyclic Jacobi solve spread over a thread-block cluster of C CTAs (C SMs).
+// On this GPU one SM retires two FP64 FMAs per clock, and the one-CTA solve above
+// saturates that pipe, so the solve is split by rows: CTA r holds rows
+// [r * rpb, (r + 1) * rpb) of G and of V in its shared memory, and the cluster
+// runs the identical rotation schedule, thresholds and truncation rule.  Each
+// round takes two cluster barriers:
+//   A  the owner of row p computes the rotation of pair (p, q) (G_qq read from
+//      q's owner through distributed shared memory) and writes it into the
+//      rotation table of every CTA;
+//      -- cluster barrier --
+//   B  rows (J^dag G): each CTA writes its rows of the next buffer, reading the
+//      partner row from its owner (the current buffer is not written in a round);
+//   C  columns (G J, V J) on its own rows of the next buffer, with the annihilated
+//      entries written as exact zeros;
+//      -- cluster barrier --
+// The eigenvalues are then gathered by every CTA, which all take the same
+// truncation decision; each CTA writes the kept vectors of its own rows.
+template <typename R>
+struct JRot {
+  R c;
+  cx<R> sp;
+  int p, q;  // p < 0: the pair is not rotated this round
+};
+
+constexpr int EIG_CL_MAX_NP = 256;
+
+template <typename R, int NT, int C>
+__global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, double* prof) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ unsigned char smem_raw[];
+  const int n = dev_eval(e.n, d);
+  const int tid = threadIdx.x;
+  const int rank = (int)cluster.block_rank();
+  if (n <= 0) {
+    if (rank == 0 && tid == 0) d[e.dim_out] = 0;
+    return;
+  }
+  const int np = n + (n & 1);
+  const int rpb = (np + C - 1) / C;
+  const int r0 = rank * rpb;
+  const int r1 = min(np, r0 + rpb);
+  const int nloc = max(0, r1 - r0);
+  cx<R>* Gb0 = (cx<R>*)smem_raw;
+  cx<R>* Gb1 = Gb0 + (long)rpb * np;
+  cx<R>* Vl = Gb1 + (long)rpb * np;
+  __shared__ JRot<R> rot[EIG_CL_MAX_NP / 2];
+  __shared__ int cnt[2];
+  __shared__ double s_part;
+  __shared__ double s_lam[EIG_CL_MAX_NP];
+  __shared__ int s_perm[EIG_CL_MAX_NP];
+  __shared__ double s_w[EIG_CL_MAX_NP];
+  __shared__ int s_k, s_bad;
+  __shared__ R s_thr;
+  __shared__ double s_tr;
+  const R zero = to_r<R>(0.0), one = to_r<R>(1.0);
+
+  const zd* G = (const zd*)e.G;
+  for (long x = tid; x < (long)nloc * np; x += NT) {
+    int li = (int)(x / np), j = (int)(x - (long)li * np);
+    int i = r0 + li;
+    zd v = mk<double>(0, 0);
+    if (i < n && j < n) v = G[(long)i * n + j];
+    if (i == j) v.im = 0;
+    Gb0[x] = mk<R>(to_r<R>(v.re), to_r<R>(v.im));
+    Vl[x] = mk<R>(to_r<R>(i == j ? 1.0 : 0.0), zero);
+  }
+  if (tid == 0) {
+    s_bad = 0;
+    cnt[0] = cnt[1] = 0;
+    double tr = 0;
+    for (int i = 0; i < n; i++) tr += fabs(G[(long)i * n + i].re);
+    s_thr = to_r<R>(0.1 * Eps<R>::v * tr);  // the same floors as the one-CTA solve
+    s_tr = tr;
+  }
+  cluster.sync();
+  const R abs_thr = s_thr;
+  const R rel_tol = to_r<R>(Eps<R>::v * (double)(n > 8 ? n : 8));
+  const int npairs = np / 2;
+  int cur = 0;
+  int sweep = 0;
+  long total_rot = 0;
+  for (; sweep < e.max_sweeps; sweep++) {
+    const int par = sweep & 1;
+    if (tid == 0) cnt[par] = 0;
+    __syncthreads();
+    for (int round = 0; round < np - 1; round++) {
+      cx<R>* Gc = cur ? Gb1 : Gb0;
+      cx<R>* Gn = cur ? Gb0 : Gb1;
+      // A: rotations of the pairs whose p row is ours, published cluster-wide
+      for (int t = tid; t < npairs; t += NT) {
+        int p = rr_player(t, round, np), q = rr_player(np - 1 - t, round, np);
+        if (p > q) {
+          int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        if (p < r0 || p >= r1) continue;
+        R c = one;
+        cx<R> sp = mk<R>(zero, zero);
+        bool rotf = false;
+        if (q < n) {
+          R a = Gc[(long)(p - r0) * np + p].re;
+          cx<R> gpq = Gc[(long)(p - r0) * np + q];
+          const int oq = q / rpb;
+          const cx<R>* Gq = cluster.map_shared_rank(Gc, oq);
+          R b = Gq[(long)(q - oq * rpb) * np + q].re;
+          R x = sqrt(cabs2(gpq));
+          if (x > rel_tol * sqrt(fabs(a * b)) && x > abs_thr && x > zero) {
+            R tau = (b - a) / (x + x);
+            R tt = fabs(tau) > to_r<R>(1e15) ? to_r<R>(0.5) / tau
+                                              : (tau >= zero ? one : -one) / (fabs(tau) + sqrt(one + tau * tau));
+            c = one / sqrt(one + tt * tt);
+            R sx = (tt * c) / x;
+            sp = mk<R>(sx * gpq.re, sx * gpq.im);
+            rotf = true;
+          }
+        }
+        JRot<R> rr;
+        rr.c = c;
+        rr.sp = sp;
+        rr.p = rotf ? p : -1;
+        rr.q = q;
+        for (int k = 0; k < C; k++) cluster.map_shared_rank(rot, k)[t] = rr;
+        if (rotf) atomicAdd(&cnt[par], 1);
+      }
+      cluster.sync();
+      // B: rows of J^dag G into the next buffer
+      for (long w = tid; w < (long)nloc * np; w += NT) {
+        const int li = (int)(w / np), j = (int)(w - (long)li * np);
+        const int i = r0 + li;
+        const int pos = i == 0 ? 0 : 1 + ((i - 1 - round) % (np - 1) + (np - 1)) % (np - 1);
+        const JRot<R> rr = rot[pos < npairs ? pos : np - 1 - pos];
+        cx<R> gi = Gc[w];
+        cx<R> out = gi;
+        if (rr.p >= 0) {
+          const int partner = i == rr.p ? rr.q : rr.p;
+          const int op = partner / rpb;
+          const cx<R> gx = cluster.map_shared_rank(Gc, op)[(long)(partner - op * rpb) * np + j];
+          out = i == rr.p ? csub(cscale(gi, rr.c), cmul(rr.sp, gx)) : cadd(cmul(cconj(rr.sp), gx), cscale(gi, rr.c));
+        }
+        Gn[w] = out;
+      }
+      __syncthreads();
+      // C: columns G J, V J on our rows; the pair's off-diagonal becomes an exact zero
+      for (long w = tid; w < (long)nloc * npairs; w += NT) {
+        const int li = (int)(w / npairs), t = (int)(w - (long)li * npairs);
+        const JRot<R> rr = rot[t];
+        if (rr.p < 0) continue;
+        const int p = rr.p, q = rr.q, i = r0 + li;
+        cx<R> gp = Gn[(long)li * np + p], gq = Gn[(long)li * np + q];
+        cx<R> np_ = csub(cscale(gp, rr.c), cmul(cconj(rr.sp), gq));
+        cx<R> nq_ = cadd(cmul(rr.sp, gp), cscale(gq, rr.c));
+        if (i == p) {
+          np_.im = zero;
+          nq_ = mk<R>(zero, zero);
+        } else if (i == q) {
+          np_ = mk<R>(zero, zero);
+          nq_.im = zero;
+        }
+        Gn[(long)li * np + p] = np_;
+        Gn[(long)li * np + q] = nq_;
+        cx<R> vp = Vl[(long)li * np + p], vq = Vl[(long)li * np + q];
+        Vl[(long)li * np + p] = csub(cscale(vp, rr.c), cmul(cconj(rr.sp), vq));
+        Vl[(long)li * np + q] = cadd(cmul(rr.sp, vp), cscale(vq, rr.c));
+      }
+      cluster.sync();
+      cur ^= 1;
+    }
+    int nr = 0;
+    for (int k = 0; k < C; k++) nr += *cluster.map_shared_rank(&cnt[par], k);
+    total_rot += nr;
+    if (nr == 0) break;
+  }
+  cx<R>* Gc = cur ? Gb1 : Gb0;
+  bool unconverged = false;
+  const bool at_limit = sweep >= e.max_sweeps;
+  if (at_limit) {
+    // accept a solve whose remaining couplings are at the rounding level
+    if (tid == 0) s_part = 0.0;
+    __syncthreads();
+    double acc = 0.0;
+    for (long x = tid; x < (long)nloc * np; x += NT) {
+      int li = (int)(x / np), j = (int)(x - (long)li * np);
+      int i = r0 + li;
+      if (i < n && j < n && i != j) acc += to_d(cabs2(Gc[x]));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((tid & 31) == 0) atomicAdd(&s_part, acc);
+    cluster.sync();
+    double off = 0.0;
+    for (int k = 0; k < C; k++) off += *cluster.map_shared_rank(&s_part, k);
+    unconverged = !(sqrt(off) <= (double)n * Eps<R>::v * s_tr);
+  }
+  // every CTA gathers the eigenvalues and takes the same truncation decision
+  for (int i = tid; i < n; i += NT) {
+    const int oi = i / rpb;
+    s_lam[i] = to_d(cluster.map_shared_rank(Gc, oi)[(long)(i - oi * rpb) * np + i].re);
+  }
+  cluster.sync();  // no CTA leaves while another still reads its shared memory
+  for (int i = tid; i < n; i += NT) {
+    double li = s_lam[i];
+    if (!isfinite(li)) s_bad = 1;
+    int rk = 0;
+    for (int j = 0; j < n; j++) {
+      double lj = s_lam[j];
+      if (lj > li || (lj == li && j < i)) rk++;
+    }
+    s_perm[rk] = i;
+  }
+  __syncthreads();
+  for (int r = tid; r < n; r += NT) {
+    double l = s_lam[s_perm[r]];
+    s_w[r] = l > 0.0 ? l : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int cap = dev_eval(e.cap, d);
+    if (cap < 1) cap = 1;
+    int k = s_bad ? 1 : keep_count_dev(s_w, n, e.tol, cap, e.gap);
+    s_k = k;
+    if (rank == 0) {
+      d[e.dim_out] = k;
+      double total = 0.0, kept = 0.0;
+      for (int i = 0; i < n; i++) total += s_w[i];
+      for (int i = 0; i < k; i++) kept += s_w[i];
+      if (e.kept_weight) *e.kept_weight = kept;
+      if (e.total_weight) *e.total_weight = total;
+      if (e.disc_stat && total > 0.0) {
+        double r = (total - kept) / total;
+        if (r > *e.disc_stat) *e.disc_stat = r;
+      }
+      if (e.lam)
+        for (int i = 0; i < n; i++) e.lam[i] = s_w[i];
+      if (e.err) {
+        if (unconverged) atomicOr(e.err, 1);
+        if (s_bad || !isfinite(total)) atomicOr(e.err, 2);
+      }
+      if (e.solver_stats) {
+        atomicAdd(e.solver_stats + 0, 1.0);
+        atomicAdd(e.solver_stats + 1, (double)(at_limit ? e.max_sweeps : sweep + 1));
+        atomicAdd(e.solver_stats + 2, (double)n);
+        atomicAdd(e.solver_stats + 3, (double)k);
+        if (at_limit) atomicAdd(e.solver_stats + 4, 1.0);
+        atomicMax((unsigned long long*)(e.solver_stats + 6), (unsigned long long)__double_as_longlong((double)n));
+      }
+      if (prof) {
+        atomicAdd(prof, 40.0 * (double)np * (double)total_rot);
+        atomicAdd(prof + QLB_K_COUNT, 2.0 * sizeof(zd) * (double)n * (double)n);
+      }
+    }
+  }
+  __syncthreads();
+  const int k = s_k;
+  zd* out = (zd*)e.out;
+  const int rl = max(0, min(r1, n) - r0);
+  if (e.out_mode == 0) {
+    for (long x = tid; x < (long)rl * k; x += NT) {
+      int li = (int)(x / k), j = (int)(x - (long)li * k);
+      cx<R> v = Vl[(long)li * np + s_perm[j]];
+      out[(long)(r0 + li) * k + j] = mk<double>(to_d(v.re), to_d(v.im));
+    }
+  } else if (e.out_mode == 1) {
+    for (long x = tid; x < (long)rl * k; x += NT) {
+      int li = (int)(x / k), j = (int)(x - (long)li * k);
+      cx<R> v = Vl[(long)li * np + s_perm[j]];
+      out[(long)j * n + (r0 + li)] = mk<double>(to_d(v.re), -to_d(v.im));
+    }
+  }
+}
+
 // One-CTA Hermitian eigen-solve by Householder tridiagonalisation and implicit QL
 // (the FP64 form at sizes whose matrices fit in shared memory).  Cyclic Jacobi
 // spends ~30 n^3 flops and 3 barriers per round over ~10 sweeps of n - 1 rounds;
@@ -635,14 +908,41 @@ constexpr size_t HEEV_SMEM_LIMIT = 160 * 1024;
 constexpr int HEEV_N_MAX = 64;
 
 size_t eig_workspace_elems(int n_max) {
+  if (n_max <= EIG_CL_MAX_NP) return 1;  // cluster solves keep everything in shared memory
   int np = n_max + (n_max & 1);
   size_t need = 2 * (size_t)np * np;
   size_t limit = n_max <= HEEV_N_MAX ? HEEV_SMEM_LIMIT : EIG_SMEM_LIMIT;
   return need * sizeof(zd) > limit ? need : 1;
 }
 
+template <typename R, int C>
+cudaError_t launch_eig_cl(const EigDesc& e, const int* d_dims, cudaStream_t s, double* prof) {
+  const int np = e.n_max + (e.n_max & 1);
+  const int rpb = (np + C - 1) / C;
+  size_t dyn = 3 * (size_t)rpb * np * sizeof(cx<R>);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_eig_cl<R, 256, C>, e, (int*)d_dims, prof);
+}
+
 template <typename R>
 cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof) {
+  // planned sizes past one SM's worth of work: the cluster solve (rows of G and V
+  // spread over 8 or 16 SMs in distributed shared memory)
+  if ((std::is_same<R, df64>::value ? e.n_max > 24 : e.n_max > HEEV_N_MAX) && e.n_max <= EIG_CL_MAX_NP) {
+    if (e.n_max <= 128) return launch_eig_cl<R, 8>(e, d_dims, s, prof);
+    return launch_eig_cl<R, 16>(e, d_dims, s, prof);
+  }
   if (std::is_same<R, double>::value && e.n_max <= HEEV_N_MAX) {
     // FP64 form, shared-memory sizes: Householder tridiagonalisation + implicit QL.
     // Past HEEV_N_MAX its matrices spill to global memory and the serial QL chain
@@ -681,6 +981,12 @@ void init_kernel_attributes() {
   set_attr<df64, 512>();
   set_attr<df64, 1024>();
   cudaFuncSetAttribute(k_heev<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HEEV_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig_cl<double, 256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig_cl<double, 256, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig_cl<double, 256, 16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_eig_cl<df64, 256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig_cl<df64, 256, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig_cl<df64, 256, 16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 }  // namespace qlb
