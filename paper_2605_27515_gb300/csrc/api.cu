@@ -128,7 +128,7 @@ qlb_state::~qlb_state() {
   if (stream) cudaStreamSynchronize(stream);
   if (graph) cudaGraphExecDestroy(graph);
   for (auto p : site) dev_free(nullptr, p);
-  for (auto p : {X, Mb, G, Cin, Cout, T1, T2, T3, eigw, oE0, oE1, oY, oZ}) dev_free(nullptr, p);
+  for (auto p : {X, Mb, G, Cin, Cout, T1, T2, T3, eigw, oE0, oE1, oY, oZ, Wsk}) dev_free(nullptr, p);
   dev_free(nullptr, d_lam);
   dev_free(nullptr, d_stats);
   dev_free(nullptr, d_err);

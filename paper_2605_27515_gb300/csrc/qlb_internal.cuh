@@ -112,6 +112,11 @@ struct GemmDesc {
   // caps on the grid (host-known maxima)
   int m_max, n_max, nb_max;
   int kclass;  // profiling class
+  // split-K: ksplit > 1 spreads the K range over ksplit CTAs per output tile; the
+  // partial sums go to ws ([ksplit][nb_max][m_max][n_max] complex) and a second
+  // kernel adds them in a fixed order and applies alpha and beta (deterministic)
+  int ksplit;
+  void* ws;
 };
 
 // Hermitian eigen solve + truncation select (one CTA per problem).

@@ -145,6 +145,10 @@ struct qlb_state {
   // transfer-sweep buffers of the observables (grown on demand, reused by later calls)
   qlb::zd *oE0 = nullptr, *oE1 = nullptr, *oY = nullptr, *oZ = nullptr;
   size_t noE = 0, noY = 0, noZ = 0;
+  // split-K of the zip-up Gram GEMMs (per site) and their partial-sum workspace
+  std::vector<int> gram_split;
+  qlb::zd* Wsk = nullptr;
+  size_t nWsk = 0;
   double* d_lam = nullptr;
   double* d_stats = nullptr;  // [0] kept weight (mu), [1] total weight (mu), [2] max disc, [3] scratch
   int* d_err = nullptr;

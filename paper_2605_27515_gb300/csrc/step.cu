@@ -648,6 +648,18 @@ qlb_status plan_buffers(qlb_state* st, const Kraus& K) {
   if ((s = realloc_buf(ctx, &st->T2, &t2, nT))) return s;
   if ((s = realloc_buf(ctx, &st->T3, &t3, nT))) return s;
   st->nT = std::max(st->nT, nT);
+  // split-K of the zip-up Grams: their (2 z) x (2 z) outputs make few 32 x 32 tiles
+  // over a long K = d D, so the K range is spread until about 64 CTAs work on it
+  st->gram_split.assign(L, 1);
+  size_t nWs = 1;
+  for (int i = 0; i + 1 < L; i++) {
+    const long mm = 2L * c.zcap[i], kk = (long)c.dcap[i + 1] * D[i + 1];
+    const long tiles = ((mm + 31) / 32) * ((mm + 31) / 32);
+    int ks = (int)std::min<long>({16, std::max<long>(1, 64 / std::max<long>(1, tiles)), std::max<long>(1, kk / 64)});
+    st->gram_split[i] = ks;
+    if (ks > 1) nWs = std::max(nWs, (size_t)ks * mm * mm);
+  }
+  if ((s = realloc_buf(ctx, &st->Wsk, &st->nWsk, nWs))) return s;
   size_t new_ew = eig_workspace_elems(n_eig);
   if ((s = realloc_buf(ctx, &st->eigw, &st->nEw, new_ew))) return s;
   if (!st->d_lam) {
@@ -881,6 +893,11 @@ qlb_status enqueue_step(qlb_state* st, const Kraus& K, bool count_step) {
     g.lda = g.ldb = dvar(SB(i + 1), Dr);
     g.ldc = dvar(ZB(st, i), 2);
     g.m_max = g.n_max = 2 * cap(ZB(st, i));
+    if (i < (int)st->gram_split.size() && st->gram_split[i] > 1 &&
+        (size_t)st->gram_split[i] * g.m_max * g.n_max <= st->nWsk) {
+      g.ksplit = st->gram_split[i];
+      g.ws = st->Wsk;
+    }
     if ((s = gemm(st, g))) return s;
     EigDesc e{};
     e.G = st->G;
