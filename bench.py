@@ -291,20 +291,23 @@ def run_gpu(args):
 
 def serving_summary(dev, n_requests, step_scale, precision, budget_gb=4.0):
     """The serving workload (Poisson arrivals at 200/s of single-cat requests,
-    seed 20260527) through the continuous-batching loop; step counts scaled by
-    step_scale so the run stays short.  Returns p50/p99 latency and steps/s."""
+    seed 20260527) through the library's continuous-batching server (qlb_server_*):
+    requests are submitted at their arrival times, step counts scaled by step_scale
+    so the run stays short.  Returns p50/p99 latency and steps/s."""
     from paper_2605_27515_gb300 import inputs, qlb, serving
 
     ctx = qlb.Ctx(device=dev, precision=precision, chi_max=64, chi_mu_max=8, stream_ordered=1)
     reqs = inputs.serving_requests(n=n_requests)
-    srv = serving.Server(ctx, hbm_budget=int(budget_gb * (1 << 30)), max_slots=64, chunk=100)
+    srv = qlb.Server(ctx, hbm_budget=int(budget_gb * (1 << 30)), max_live=64, chunk=100)
     t0 = time.perf_counter()
-    jobs = srv.run(reqs, step_scale=step_scale)
+    jobs = serving.drive(srv, reqs, step_scale=step_scale)
     wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
     out = serving.summarize(jobs, wall)
-    out.update({"workload": "serving", "step_scale": step_scale, "peak_live": srv.peak_live,
-                "peak_device_bytes": srv.peak_bytes, "hbm_budget_bytes": int(budget_gb * (1 << 30)),
-                "arrivals": "Poisson 200/s, seed 20260527"})
+    out.update({"workload": "serving", "step_scale": step_scale, "peak_live": stats["peak_live"],
+                "peak_device_bytes": stats["peak_bytes"], "hbm_budget_bytes": int(budget_gb * (1 << 30)),
+                "arrivals": "Poisson 200/s, seed 20260527", "engine": "qlb_server (C-ABI)"})
     ctx.close()
     return out
 

@@ -66,6 +66,12 @@ typedef struct qlb_state qlb_state;
 #define QLB_PREC_MIXED 1 /* the Jacobi truncation solves in double-float (pairs of FP32,
                             ~48-bit significands) on the FP32 pipes; contractions, Gram
                             matrices, truncation decisions and renormalisation in FP64 */
+#define QLB_PREC_TC 2    /* QLB_PREC_MIXED with the MPO application (the two zip-up
+                            contractions of every site) on the tensor cores in 3xTF32
+                            (operands split into two TF32 parts, FP32 accumulation);
+                            Gram matrices, truncation decisions and renormalisation stay
+                            FP64 (Sec. V.A MPO.MPS product; precision split of the
+                            contractions only) */
 
 typedef struct {
   int device;            /* CUDA device ordinal */
@@ -250,6 +256,58 @@ qlb_status qlb_kraus_to_dense(qlb_state* st, double dt, int k, double* out, size
 qlb_status qlb_state_export(qlb_state* st, void* out, size_t cap, size_t* n_bytes);
 qlb_status qlb_state_import(qlb_state* st, const void* in, size_t n_bytes);
 
+/* ------------------------------------------------------------------ serving */
+
+/* Continuous-batching service of independent solves on one GPU (the serving
+ * workload: requests of differing mode counts, Fock sizes and bond caps arriving
+ * over time).  A server takes over its context: while it exists only its worker
+ * thread issues device work on that context (the caller must not use the context,
+ * its systems or states meanwhile).  The worker admits pending requests in
+ * arrival order while fewer than max_live are running and the request's
+ * estimated device memory fits hbm_budget (0: no limit) next to the running ones;
+ * it builds the request's system and state, steps every running state in chunks
+ * of `chunk` steps on the state's own stream (the chunks of different requests
+ * overlap on the GPU), evaluates the request's observables when its steps are
+ * done, and releases its memory and slot.  The context must be created with
+ * stream_ordered = 1. */
+typedef struct qlb_server qlb_server;
+
+/* One solve.  Every array is copied at qlb_submit (dense factors included). */
+typedef struct {
+  int n_modes;                     /* 1..16 */
+  const int* R;                    /* N_m = 2^R[m] */
+  const qlb_term* H;               /* time-independent Hamiltonian terms (n_H may be 0) */
+  int n_H;
+  const qlb_term* const* jumps;    /* jumps[k]: the n_jump_terms[k] terms of L_k */
+  const int* n_jump_terms;
+  int n_jumps;
+  const double* const* mode_vecs;  /* product start: N_m complex128 per mode */
+  double dt;                       /* first-order Kraus step (Sec. V.B) */
+  int64_t steps;
+  double tol;                      /* truncation of this request; <= 0: the context's */
+  int chi_max;                     /* <= the context's chi_max; <= 0: the context's */
+  int chi_mu_max;                  /* <= the context's chi_mu_max; <= 0: the context's */
+  const qlb_term* const* obs;      /* observables: Tr(O rho) at completion */
+  const int* n_obs_terms;
+  int n_obs;
+} qlb_request;
+
+qlb_status qlb_server_create(qlb_ctx* ctx, size_t hbm_budget, int max_live, int chunk, qlb_server** out);
+/* Stops the worker (running requests are dropped) and frees the server. */
+void qlb_server_destroy(qlb_server* srv);
+/* Queues a request; *ticket identifies it.  QLB_EINVAL for malformed requests. */
+qlb_status qlb_submit(qlb_server* srv, const qlb_request* req, int64_t* ticket);
+/* QLB_BUSY while the request is pending or running.  Once done: QLB_OK with
+ * results = (re, im) of each observable (cap doubles at most) and times3 = seconds
+ * since the server was created at arrival, admission and completion; a failed
+ * request returns its error status, a cancelled one QLB_ESTATE. */
+qlb_status qlb_poll(qlb_server* srv, int64_t ticket, double* results, int cap, double* times3);
+/* Cancels a pending or running request (a running one stops between two chunks). */
+qlb_status qlb_cancel(qlb_server* srv, int64_t ticket);
+/* out6 = [running, peak running, peak device bytes of the context, completed,
+ * steps taken, pending]. */
+qlb_status qlb_server_stats(qlb_server* srv, double* out6);
+
 /* ------------------------------------------------------------------ profiling */
 
 /* Kernel classes for qlb_profile_read. */
@@ -282,6 +340,13 @@ qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out, int n_out);
  * CUDA events, best of three ~20 ms launches).  The denominators of the
  * truncation solvers' roofline.  Allocates a few KB for the duration of the call. */
 qlb_status qlb_measure_peak(int device, int kind, double* tflops);
+
+/* C = A B for host row-major complex128 matrices (A m x k, B k x n, C m x n) through
+ * the tensor-core engine of QLB_PREC_TC: the same 3xTF32 tcgen05 GEMM the mixed form
+ * applies the Kraus MPO with (Sec. V.A), exposed so that its numerics can be checked
+ * against an FP64 product.  Copies the operands to device `device`, allocating for the
+ * duration of the call.  QLB_ETIMEOUT if a bounded wait of the kernel gave up. */
+qlb_status qlb_tc_zgemm(int device, int m, int n, int k, const double* A, const double* B, double* C);
 
 #ifdef __cplusplus
 }

@@ -172,7 +172,8 @@ QLB_API qlb_status qlb_create(const qlb_options* opt, qlb_ctx** out) {
     o = *opt;
   else
     qlb_default_options(&o);
-  CHECK_ARG(o.precision == QLB_PREC_F64 || o.precision == QLB_PREC_MIXED, "unknown precision");
+  CHECK_ARG(o.precision == QLB_PREC_F64 || o.precision == QLB_PREC_MIXED || o.precision == QLB_PREC_TC,
+            "unknown precision");
   CHECK_ARG(o.tol >= 0 && o.tol < 1, "tol must be in [0, 1)");
   CHECK_ARG(o.chi_max >= 1 && o.chi_max <= 256, "chi_max must be in [1, 256]");
   CHECK_ARG(o.chi_mu_max >= 1 && o.chi_mu_max <= 128, "chi_mu_max must be in [1, 128]");
@@ -195,6 +196,7 @@ QLB_API qlb_status qlb_create(const qlb_options* opt, qlb_ctx** out) {
     return QLB_EDEVICE;
   }
   init_kernel_attributes();
+  init_tc_attributes();
   {
     qlb_status st = dev_alloc(c, (void**)&c->d_solver, sizeof(double) * 8);
     if (st == QLB_OK && cudaMemset(c->d_solver, 0, sizeof(double) * 8) != cudaSuccess) st = QLB_EDEVICE;
@@ -927,5 +929,71 @@ QLB_API qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out, int n_out
   double h[8] = {0};
   if (ctx->d_solver) QLB_CUDA_TRY(cudaMemcpy(h, ctx->d_solver, sizeof(h), cudaMemcpyDeviceToHost));
   for (int i = 0; i < n_out && i < 7; i++) out[i] = h[i];
+  return QLB_OK;
+}
+
+// ------------------------------------------------------------------ tensor-core GEMM check
+
+QLB_API qlb_status qlb_tc_zgemm(int device, int m, int n, int k, const double* A, const double* B, double* C) {
+  CHECK_ARG(A && B && C, "null argument");
+  CHECK_ARG(m >= 1 && n >= 1 && k >= 0 && (long)m * n <= (1L << 26) && (long)m * k <= (1L << 26) &&
+                (long)k * n <= (1L << 26),
+            "sizes out of range");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    set_error("qlb_tc_zgemm: no such CUDA device");
+    return QLB_EDEVICE;
+  }
+  QLB_CUDA_TRY(cudaSetDevice(device));
+  init_tc_attributes();
+  zd *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  int* derr = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dC);
+    cudaFree(derr);
+  };
+  if (cudaMalloc(&dA, sizeof(zd) * std::max<long>(1, (long)m * k)) != cudaSuccess ||
+      cudaMalloc(&dB, sizeof(zd) * std::max<long>(1, (long)k * n)) != cudaSuccess ||
+      cudaMalloc(&dC, sizeof(zd) * (long)m * n) != cudaSuccess || cudaMalloc(&derr, sizeof(int)) != cudaSuccess) {
+    cleanup();
+    set_error("qlb_tc_zgemm: device allocation failed");
+    return QLB_ENOMEM;
+  }
+  cudaMemcpy(dA, A, sizeof(zd) * (long)m * k, cudaMemcpyHostToDevice);
+  cudaMemcpy(dB, B, sizeof(zd) * (long)k * n, cudaMemcpyHostToDevice);
+  cudaMemset(derr, 0, sizeof(int));
+  GemmDesc g{};
+  g.A = dA;
+  g.B = dB;
+  g.C = dC;
+  g.m = dconst(m);
+  g.n = dconst(n);
+  g.k = dconst(k);
+  g.lda = dconst(k);
+  g.ldb = dconst(n);
+  g.ldc = dconst(n);
+  g.sA1 = g.sB1 = g.sC1 = g.sA2 = g.sB2 = g.sC2 = dconst(0);
+  g.nb1 = g.nb2 = dconst(1);
+  g.alpha_re = 1.0;
+  g.m_max = m;
+  g.n_max = n;
+  g.nb_max = 1;
+  cudaError_t e = launch_gemm_tc(g, nullptr, 0, derr, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(C, dC, sizeof(zd) * (long)m * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+  cleanup();
+  if (e != cudaSuccess) {
+    set_error(std::string("qlb_tc_zgemm: ") + cudaGetErrorString(e));
+    return QLB_EDEVICE;
+  }
+  if (herr) {
+    set_error("qlb_tc_zgemm: a bounded wait for the tensor-core pipeline gave up");
+    return QLB_ETIMEOUT;
+  }
   return QLB_OK;
 }

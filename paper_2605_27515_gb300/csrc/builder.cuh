@@ -22,6 +22,11 @@ size_t eig_smem_bytes(int n_max);
 // device workspace (complex elements) the eigen-solvers need beyond shared memory
 size_t eig_workspace_elems(int n_max);
 void init_kernel_attributes();
+// 3xTF32 complex GEMM on the tensor cores (same descriptor as launch_gemm); err bit 2
+// is set when a bounded wait of the kernel gave up
+cudaError_t launch_gemm_tc(const GemmDesc& g, const int* d_dims, cudaStream_t s, int* err, double* prof);
+size_t tc_gemm_smem_bytes();
+void init_tc_attributes();
 
 qlb_status svd_osj(qlb_ctx* ctx, zd* X, int m, int n, double tol, int cap, zd** U, int u_scale, zd** Rr,
                    int r_unscale, int* k_out, int max_sweeps);

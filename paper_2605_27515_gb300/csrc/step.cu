@@ -210,7 +210,12 @@ static qlb_status gemm(qlb_state* st, GemmDesc& g) {
   qlb_ctx* ctx = st->sys->ctx;
   cudaEvent_t a;
   prof_before(ctx, st->stream, g.kclass, &a);
-  cudaError_t e = launch_gemm<double>(g, st->d_dims, st->stream, ctx->prof_on ? ctx->d_prof + g.kclass : nullptr);
+  double* pf = ctx->prof_on ? ctx->d_prof + g.kclass : nullptr;
+  // the tensor-core form runs the MPO application (the zip-up contractions) in
+  // 3xTF32 on tcgen05; everything feeding a truncation decision stays FP64
+  cudaError_t e = (st->prec == QLB_PREC_TC && g.kclass == QLB_K_CONTRACT)
+                      ? launch_gemm_tc(g, st->d_dims, st->stream, st->d_err, pf)
+                      : launch_gemm<double>(g, st->d_dims, st->stream, pf);
   prof_after(ctx, st->stream, g.kclass, a);
   if (e != cudaSuccess) {
     set_error(std::string("gemm launch: ") + cudaGetErrorString(e));
@@ -227,8 +232,8 @@ static qlb_status eig(qlb_state* st, EigDesc& e) {
   double* pf = ctx->prof_on ? ctx->d_prof + QLB_K_EIG : nullptr;
   e.solver_stats = ctx->d_solver;
   // the mixed form runs the same Jacobi in double-float on the FP32 pipes
-  cudaError_t r = st->prec == QLB_PREC_MIXED ? launch_eig<df64>(e, st->d_dims, st->stream, st->eigw, pf)
-                                             : launch_eig<double>(e, st->d_dims, st->stream, st->eigw, pf);
+  cudaError_t r = st->prec != QLB_PREC_F64 ? launch_eig<df64>(e, st->d_dims, st->stream, st->eigw, pf)
+                                           : launch_eig<double>(e, st->d_dims, st->stream, st->eigw, pf);
   prof_after(ctx, st->stream, QLB_K_EIG, a);
   if (r != cudaSuccess) {
     set_error(std::string("eig launch: ") + cudaGetErrorString(r));
@@ -983,6 +988,10 @@ qlb_status run_steps(qlb_state* st, int64_t n, bool sync) {
   QLB_CUDA_TRY(cudaMemcpy(&err, st->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (err) {
     QLB_CUDA_TRY(cudaMemset(st->d_err, 0, sizeof(int)));
+    if (err & 4) {
+      set_error("a bounded wait of the tensor-core contraction gave up");
+      return QLB_ETIMEOUT;
+    }
     if (err & 2) {
       set_error("non-finite values met in a truncation");
       return QLB_ENONFINITE;

@@ -17,8 +17,9 @@ _lib = None
 
 # status codes and constants (mirror of include/qlb.h)
 OK, WUNSTABLE = 0, 1
+QLB_BUSY = 2
 EINVAL, ENOMEM, ENOTCONV, ETIMEOUT, ENONFINITE, EDEVICE, ESTATE = -1, -2, -3, -4, -5, -6, -7
-PREC_F64, PREC_MIXED = 0, 1
+PREC_F64, PREC_MIXED, PREC_TC = 0, 1, 2
 F_ID, F_A, F_ADAG, F_NUM, F_PARITY, F_CHARGE, F_COSPHI, F_DENSE = range(8)
 K_CONTRACT, K_GRAM, K_EIG, K_APPLY, K_OTHER, K_COUNT = range(6)
 K_NAMES = ["contract", "gram", "eig", "apply", "other"]
@@ -47,6 +48,16 @@ class qlb_term(C.Structure):
     _fields_ = [("re", C.c_double), ("im", C.c_double), ("factors", C.POINTER(qlb_factor)), ("n_factors", C.c_int)]
 
 
+class qlb_request(C.Structure):
+    _fields_ = [
+        ("n_modes", C.c_int), ("R", C.POINTER(C.c_int)), ("H", C.POINTER(qlb_term)), ("n_H", C.c_int),
+        ("jumps", C.POINTER(C.POINTER(qlb_term))), ("n_jump_terms", C.POINTER(C.c_int)), ("n_jumps", C.c_int),
+        ("mode_vecs", C.POINTER(C.POINTER(C.c_double))), ("dt", C.c_double), ("steps", C.c_int64),
+        ("tol", C.c_double), ("chi_max", C.c_int), ("chi_mu_max", C.c_int),
+        ("obs", C.POINTER(C.POINTER(qlb_term))), ("n_obs_terms", C.POINTER(C.c_int)), ("n_obs", C.c_int),
+    ]
+
+
 _vp = C.c_void_p
 _st = C.c_int32
 _SIGS = {
@@ -62,6 +73,8 @@ _SIGS = {
     "qlb_ctx_alloc_count": (_st, [_vp, C.POINTER(C.c_int64)]),
     "qlb_profile_solver_stats": (_st, [_vp, C.POINTER(C.c_double), C.c_int]),
     "qlb_measure_peak": (_st, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "qlb_tc_zgemm": (_st, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                           C.POINTER(C.c_double)]),
     "qlb_system_create": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "qlb_system_destroy": (None, [_vp]),
     "qlb_op_build": (_st, [_vp, C.POINTER(qlb_term), C.c_int, C.c_double, C.c_int, C.POINTER(_vp)]),
@@ -86,6 +99,12 @@ _SIGS = {
     "qlb_kraus_to_dense": (_st, [_vp, C.c_double, C.c_int, C.POINTER(C.c_double), C.c_size_t]),
     "qlb_state_export": (_st, [_vp, _vp, C.c_size_t, C.POINTER(C.c_size_t)]),
     "qlb_state_import": (_st, [_vp, _vp, C.c_size_t]),
+    "qlb_server_create": (_st, [_vp, C.c_size_t, C.c_int, C.c_int, C.POINTER(_vp)]),
+    "qlb_server_destroy": (None, [_vp]),
+    "qlb_submit": (_st, [_vp, C.POINTER(qlb_request), C.POINTER(C.c_int64)]),
+    "qlb_poll": (_st, [_vp, C.c_int64, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double)]),
+    "qlb_cancel": (_st, [_vp, C.c_int64]),
+    "qlb_server_stats": (_st, [_vp, C.POINTER(C.c_double)]),
     "qlb_profile_enable": (_st, [_vp, C.c_int]),
     "qlb_profile_read": (_st, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                C.POINTER(C.c_double)]),
@@ -201,6 +220,32 @@ def qlb_measure_peak(device: int, kind: int) -> float:
 # ---------------------------------------------------------------- systems and operators
 
 
+def _terms_to_c(terms, keep):
+    """A term list as a C qlb_term array; the arrays it points at go into `keep`."""
+    cterms = (qlb_term * max(1, len(terms)))()
+    for t, (coeff, facs) in enumerate(terms):
+        cf = (qlb_factor * max(1, len(facs)))()
+        for j, f in enumerate(facs):
+            mode, kind = int(f[0]), int(f[1])
+            cf[j].mode, cf[j].kind, cf[j].power, cf[j].param = mode, kind, 1, 0.0
+            if kind == F_DENSE:
+                a, p = _cvec(f[2])
+                keep.append(a)
+                cf[j].dense = p
+            else:
+                if len(f) > 2:
+                    cf[j].power = int(f[2])
+                if len(f) > 3:
+                    cf[j].param = float(f[3])
+        keep.append(cf)
+        c = complex(coeff)
+        cterms[t].re, cterms[t].im = c.real, c.imag
+        cterms[t].factors = C.cast(cf, C.POINTER(qlb_factor))
+        cterms[t].n_factors = len(facs)
+    keep.append(cterms)
+    return cterms
+
+
 class System:
     def __init__(self, ctx: Ctx, R):
         self.ctx = ctx
@@ -220,26 +265,7 @@ class System:
         """terms: list of (coeff, [factor, ...]) with factor = (mode, kind[, power[, param]])
         or (mode, F_DENSE, matrix)."""
         keep = []
-        cterms = (qlb_term * len(terms))()
-        for t, (coeff, facs) in enumerate(terms):
-            cf = (qlb_factor * max(1, len(facs)))()
-            for j, f in enumerate(facs):
-                mode, kind = int(f[0]), int(f[1])
-                cf[j].mode, cf[j].kind, cf[j].power, cf[j].param = mode, kind, 1, 0.0
-                if kind == F_DENSE:
-                    a, p = _cvec(f[2])
-                    keep.append(a)
-                    cf[j].dense = p
-                else:
-                    if len(f) > 2:
-                        cf[j].power = int(f[2])
-                    if len(f) > 3:
-                        cf[j].param = float(f[3])
-            keep.append(cf)
-            c = complex(coeff)
-            cterms[t].re, cterms[t].im = c.real, c.imag
-            cterms[t].factors = C.cast(cf, C.POINTER(qlb_factor))
-            cterms[t].n_factors = len(facs)
+        cterms = _terms_to_c(terms, keep)
         h = _vp()
         _check(self.lib.qlb_op_build(self.h, cterms, len(terms), float(tol), int(chi_max), C.byref(h)))
         return Op(self, h)
@@ -386,4 +412,84 @@ class State:
     def close(self):
         if self.h:
             self.lib.qlb_state_destroy(self.h)
+            self.h = None
+
+
+def qlb_tc_zgemm(device: int, A, B) -> np.ndarray:
+    """A @ B (complex128) through the tensor-core 3xTF32 engine of the mixed form."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.complex128))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.complex128))
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2
+    Cm = np.zeros((m, n), dtype=np.complex128)
+    dp = C.POINTER(C.c_double)
+    _check(load().qlb_tc_zgemm(int(device), m, n, k, A.ctypes.data_as(dp), B.ctypes.data_as(dp),
+                               Cm.ctypes.data_as(dp)))
+    return Cm
+
+
+class Server:
+    """The library's continuous-batching server (qlb_server_*): takes over the context
+    (created with stream_ordered=1) until close()."""
+
+    def __init__(self, ctx: Ctx, hbm_budget=0, max_live=64, chunk=100):
+        self.ctx, self.lib = ctx, ctx.lib
+        h = _vp()
+        _check(self.lib.qlb_server_create(ctx.h, int(hbm_budget), int(max_live), int(chunk), C.byref(h)))
+        self.h = h
+        self.n_obs = {}
+
+    def submit(self, R, H, jumps, vecs, dt, steps, obs, tol=0.0, chi_max=0, chi_mu_max=0) -> int:
+        """H, each jump and each observable are term lists as for System.op; vecs are
+        the product-start mode vectors.  Returns the ticket."""
+        keep = []
+        req = qlb_request()
+        Rs = (C.c_int * len(R))(*[int(r) for r in R])
+        keep.append(Rs)
+        req.n_modes, req.R = len(R), Rs
+        if H:
+            req.H, req.n_H = _terms_to_c(H, keep), len(H)
+        jl = (C.POINTER(qlb_term) * max(1, len(jumps)))(*[_terms_to_c(j, keep) for j in jumps])
+        jn = (C.c_int * max(1, len(jumps)))(*[len(j) for j in jumps])
+        ol = (C.POINTER(qlb_term) * max(1, len(obs)))(*[_terms_to_c(o, keep) for o in obs])
+        on = (C.c_int * max(1, len(obs)))(*[len(o) for o in obs])
+        keep += [jl, jn, ol, on]
+        req.jumps, req.n_jump_terms, req.n_jumps = jl, jn, len(jumps)
+        req.obs, req.n_obs_terms, req.n_obs = ol, on, len(obs)
+        arrs = [_cvec(v) for v in vecs]
+        vp = (C.POINTER(C.c_double) * len(arrs))(*[p for _, p in arrs])
+        keep += [arrs, vp]
+        req.mode_vecs = vp
+        req.dt, req.steps, req.tol = float(dt), int(steps), float(tol)
+        req.chi_max, req.chi_mu_max = int(chi_max), int(chi_mu_max)
+        t = C.c_int64()
+        _check(self.lib.qlb_submit(self.h, C.byref(req), C.byref(t)))
+        self.n_obs[t.value] = len(obs)
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending or running; else (list of complex observables, (arrival,
+        admit, done) seconds).  Raises QlbError for a failed or cancelled request."""
+        n = self.n_obs.get(ticket, 0)
+        res = (C.c_double * max(2, 2 * n))()
+        tm = (C.c_double * 3)()
+        st = self.lib.qlb_poll(self.h, int(ticket), res, 2 * n, tm)
+        if st == QLB_BUSY:
+            return None
+        _check(st)
+        return [complex(res[2 * k], res[2 * k + 1]) for k in range(n)], (tm[0], tm[1], tm[2])
+
+    def cancel(self, ticket):
+        _check(self.lib.qlb_cancel(self.h, int(ticket)))
+
+    def stats(self):
+        out = (C.c_double * 6)()
+        _check(self.lib.qlb_server_stats(self.h, out))
+        return dict(live=int(out[0]), peak_live=int(out[1]), peak_bytes=int(out[2]), completed=int(out[3]),
+                    steps=int(out[4]), pending=int(out[5]))
+
+    def close(self):
+        if self.h:
+            self.lib.qlb_server_destroy(self.h)
             self.h = None

@@ -268,12 +268,12 @@ def test_drive_table_matches_dense(ctx):
 # ------------------------------------------------------------------ the cat configuration (truncated)
 
 
-@pytest.mark.parametrize("precision,nsteps", [(Q.PREC_F64, 5000), (Q.PREC_MIXED, 1500)])
+@pytest.mark.parametrize("precision,nsteps", [(Q.PREC_F64, 5000), (Q.PREC_MIXED, 5000), (Q.PREC_TC, 5000)])
 def test_cat_r5_parity_full_run(precision, nsteps):
     """Single cat mode, N = 32, dt = 1e-3, cutoff 1e-12, chi_mu <= 8: photon number
-    and parity within 1e-6 of the dense oracle every 100 steps; the whole 5000-step
-    run in the FP64 form, its first 1500 steps in the mixed form (double-float
-    truncation solves)."""
+    and parity within 1e-6 of the dense oracle every 100 steps over the whole
+    5000-step run, in the FP64 form, the mixed form (double-float truncation solves)
+    and the tensor-core form (3xTF32 MPO application on tcgen05 as well)."""
     cfg = inputs.config("cat_r5")
     cfg["steps"] = nsteps
     c = Q.Ctx(device=0, precision=precision, tol=cfg["tol"], chi_max=cfg["chi_max"], chi_mu_max=cfg["chi_mu_max"])

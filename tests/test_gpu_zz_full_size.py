@@ -23,7 +23,7 @@ def oracle_records():
     return recs
 
 
-@pytest.mark.parametrize("precision", [Q.PREC_F64, Q.PREC_MIXED])
+@pytest.mark.parametrize("precision", [Q.PREC_F64, Q.PREC_MIXED, Q.PREC_TC])
 def test_full_size_first_steps_match_oracle(oracle_records, precision):
     cfg = inputs.config("cat_r9")
     ctx = Q.Ctx(device=0, precision=precision, tol=cfg["tol"], chi_max=cfg["chi_max"],

@@ -1,117 +1,70 @@
-"""Host logic of the serving loop (admission by memory budget and slots, arrival
-order, chunked stepping, completion) with stand-in states, no GPU."""
+"""Host side of the serving workload (no GPU): the request marshalling into term
+lists, the arrival driver (submission at the arrival times, polling until every
+request is done, step scaling) against a stand-in server, and the summary."""
 import numpy as np
 
+from paper_2605_27515_gb300 import inputs
+from paper_2605_27515_gb300 import qlb as Q
 from paper_2605_27515_gb300 import serving
 
 
-class _Opts:
-    chi_max = 64
-    chi_mu_max = 8
-
-
-class _Ctx:
-    opts = _Opts()
-
-    def memory(self):
-        return 0
-
-
-class _Op:
-    def close(self):
-        pass
-
-
-class _State:
-    """Finishes each enqueued chunk after `lag` polls, like a stream that is busy."""
-
-    def __init__(self, log, rid, lag=2):
-        self.log, self.rid, self.lag = log, rid, lag
-        self.busy = 0
-        self.steps = 0
-
-    def poll(self):
-        if self.busy:
-            self.busy -= 1
-            return False
-        return True
-
-    def step(self, dt, n):
-        assert self.busy == 0, "a chunk was enqueued on a busy state"
-        self.steps += n
-        self.busy = self.lag
-        self.log.append(("step", self.rid, n))
-
-    def expectation(self, op):
-        return complex(self.steps)
-
-    def bond_dims(self):
-        return [1]
-
-    def close(self):
-        self.log.append(("close", self.rid))
-
-
-class _Sys:
-    def close(self):
-        pass
-
-
-class _Built:
+class _Clock:
     def __init__(self):
-        self.sys = _Sys()
-        self.ops = {"L": _Op()}
-        self.observables = {"n": _Op(), "parity": _Op()}
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, s):
+        self.t += s
 
 
-def _requests(n, steps):
-    return [dict(id=i, arrival_s=0.0, R=6, alpha2=4.0, k1_over_k2=1e-3, steps=steps, dt=1e-3, chi_max=32,
-                 chi_mu_max=8, tol=1e-12) for i in range(n)]
+class _FakeServer:
+    """Finishes each request `lag` polls after its submission; records the order."""
+
+    def __init__(self, clock, lag=3):
+        self.clock, self.lag = clock, lag
+        self.log = []
+        self.jobs = {}
+
+    def submit(self, R, H, jumps, vecs, dt, steps, obs, tol=0.0, chi_max=0, chi_mu_max=0):
+        t = len(self.log)
+        self.log.append((self.clock(), R, steps, len(jumps), len(obs)))
+        self.jobs[t] = [self.lag, steps]
+        return t
+
+    def poll(self, t):
+        j = self.jobs[t]
+        if j[0] > 0:
+            j[0] -= 1
+            return None
+        return [complex(j[1]), complex(1.0)], (0.0, 0.0, 0.0)
 
 
-def _server(log, **kw):
-    def build(ctx, r):
-        log.append(("start", r["id"]))
-        return _Built(), _State(log, r["id"])
+def test_cat_request_terms():
+    r = inputs.serving_requests(n=1)[0]
+    q = serving.cat_request(r)
+    assert q["R"] == [r["R"]] and q["H"] == [] and len(q["jumps"]) == 2
+    (c1, f1), (c0, f0) = q["jumps"][0]
+    assert f1 == [(0, Q.F_A, 2)] and f0 == [] and abs(c0 + r["alpha2"]) < 1e-15 and c1 == 1.0
+    assert abs(q["jumps"][1][0][0] - np.sqrt(r["k1_over_k2"])) < 1e-15
+    assert q["vecs"][0][0] == 1.0 and np.sum(np.abs(q["vecs"][0])) == 1.0
+    assert [o[0][1][0][1] for o in q["obs"]] == [Q.F_NUM, Q.F_PARITY]
 
-    return serving.Server(_Ctx(), build=build, **kw)
 
-
-def test_every_request_completes_with_all_its_steps():
-    log = []
-    srv = _server(log, chunk=7)
-    jobs = srv.run(_requests(5, 30), step_scale=1.0, time_scale=0.0)
-    assert sorted(j.req["id"] for j in jobs) == list(range(5))
+def test_drive_submits_at_arrival_and_collects_everything():
+    reqs = inputs.serving_requests(n=12, seed=3)
+    clk = _Clock()
+    srv = _FakeServer(clk)
+    jobs = serving.drive(srv, reqs, step_scale=0.01, time_scale=1.0, poll_s=1e-3, clock=clk, sleep=clk.sleep)
+    assert len(jobs) == 12 and len(srv.log) == 12
+    # submitted in arrival order, never before the arrival time
+    times = [t for t, *_ in srv.log]
+    assert times == sorted(times)
     for j in jobs:
-        assert j.result["n"] == 30  # the stand-in reports the steps it took
-        chunks = [e[2] for e in log if e[0] == "step" and e[1] == j.req["id"]]
-        assert chunks == [7, 7, 7, 7, 2]
-    assert srv.peak_live == 5
-
-
-def test_budget_limits_live_requests():
-    log = []
-    one = serving.estimate_bytes(6, 64, 8)
-    srv = _server(log, hbm_budget=2 * one + 1, chunk=10)
-    jobs = srv.run(_requests(6, 25), step_scale=1.0, time_scale=0.0)
-    assert len(jobs) == 6 and srv.peak_live == 2
-    live = 0
-    for e in log:  # never more than two started and not yet closed
-        live += {"start": 1, "close": -1}.get(e[0], 0)
-        assert live <= 2
-
-
-def test_slots_and_arrival_order():
-    log = []
-    srv = _server(log, max_slots=1, chunk=100)
-    reqs = _requests(3, 5)
-    for r, t in zip(reqs, (0.0, 0.002, 0.004)):
-        r["arrival_s"] = t
-    jobs = srv.run(reqs, step_scale=1.0, time_scale=1.0)
-    starts = [e[1] for e in log if e[0] == "start"]
-    assert starts == [0, 1, 2] and srv.peak_live == 1
-    assert all(np.isfinite(j.done - j.arrival) and j.done >= j.arrival for j in jobs)
-
-
-def test_estimate_grows_with_caps():
-    assert serving.estimate_bytes(9, 64, 16) > serving.estimate_bytes(9, 32, 8) > 0
+        assert j.submitted >= j.arrival - 1e-12
+        assert j.done >= j.submitted
+        assert j.steps == max(10, int(j.req["steps"] * 0.01))
+        assert j.result["n"] == float(j.steps)  # the stand-in returns the step count
+    s = serving.summarize(jobs, clk.t)
+    assert s["requests"] == 12 and s["p99_latency_s"] >= s["p50_latency_s"] > 0
