@@ -331,8 +331,9 @@ qlb_status qlb_profile_reset(qlb_ctx* ctx);
  * min(n_out, 7) of: out[0] solves, out[1] Jacobi sweeps plus QL passes, out[2] sum
  * of the runtime matrix sizes n, out[3] sum of the kept counts k, out[4] solves
  * that reached the sweep (or QL iteration) limit, out[5] solves whose matrices did
- * not fit in shared memory (global-memory workspace), out[6] the largest runtime
- * size n.  Synchronises the device. */
+ * not fit in one CTA's shared memory (spread over a thread-block cluster, or in a
+ * global-memory workspace), out[6] the largest runtime size n.  Synchronises the
+ * device. */
 qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out, int n_out);
 
 /* Measured fused multiply-add throughput of device `device` in TFLOP/s:

@@ -181,7 +181,7 @@ class Ctx:
         out = (C.c_double * 7)()
         _check(self.lib.qlb_profile_solver_stats(self.h, out, 7))
         return dict(solves=out[0], sweeps=out[1], sum_n=out[2], sum_k=out[3], at_limit=out[4],
-                    global_ws=out[5], max_n=out[6])
+                    global_ws=out[5], max_n=out[6])  # global_ws: solves beyond one CTA's shared memory
 
     def profile_enable(self, on=True):
         _check(self.lib.qlb_profile_enable(self.h, int(on)))

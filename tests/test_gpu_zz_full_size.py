@@ -4,7 +4,7 @@ chi <= 64, chi_mu <= 16, cutoff 1e-12, stream-ordered context), against the dens
 FP64 oracle at N = 512 every 5 steps over the first 30, in both precision forms;
 plus properties that hold at any size (trace, purity, parity range, caps, and the
 explicit scheme's instability warning for this step size), and the solver counters
-showing that the eigen-solves reached size 128 in global memory.  Kept in a file of its
+showing that the eigen-solves reached size 128 on the multi-SM (cluster) path.  Kept in a file of its
 own, collected after the other GPU parity files."""
 import pytest
 
@@ -48,7 +48,7 @@ def test_full_size_first_steps_match_oracle(oracle_records, precision):
     assert worst < 1e-6, worst
     sv = ctx.solver_stats()
     # the zip-up bonds reach the cap of 64, so the eigen-solves run at 2 x 64 = 128,
-    # past the shared-memory sizes (the global-memory workspace path)
+    # past one CTA's shared memory (the thread-block cluster path)
     assert sv["max_n"] >= 128, sv
     assert sv["global_ws"] >= 1, sv
     st.close()
