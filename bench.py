@@ -87,6 +87,30 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def _traffic(kernel_class):
+    """DRAM bytes per launch of the class's dominant kernel from the committed ncu
+    summary (profiles/traffic.json), or None when that summary was taken on another
+    version of the kernel's source (its sha256 no longer matches)."""
+    import hashlib
+
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None, None
+    with open(p) as f:
+        tab = json.load(f)
+    ent = tab.get(kernel_class)
+    if not ent:
+        return None, None
+    src = os.path.join(ROOT, ent["source"])
+    if not os.path.exists(src):
+        return None, None
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    if sha != ent["source_sha256"]:
+        return None, f"{ent['kernel']}: source changed since the ncu capture"
+    return ent["dram_bytes_per_launch"], f"{ent['kernel']} ({ent['capture']})"
+
+
 def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -229,8 +253,9 @@ def run_gpu(args):
     # them in double-float on the FP32 pipe (its flops are counted in FP64 terms)
     peak = fp64_peak if args.precision == 0 or dom != "eig" else fp32_peak
     achieved = dp["flops"] / (dp["ms"] / 1e3) / 1e12 if dp["ms"] > 0 else 0.0
+    traffic, traffic_src = _traffic(dom)
     roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
                 "peak_source": ("measured FP64 FMA throughput of this GPU (qlb_measure_peak)"
                                 if peak == fp64_peak else "measured FP32 FMA throughput of this GPU"),
                 "launches": dp["launches"], "ms_per_launch": dp["ms"] / max(1, dp["launches"]),
@@ -241,6 +266,32 @@ def run_gpu(args):
     solver_line = {"solves_per_step": solver["solves"] / args.steps, "sweeps_per_solve": solver["sweeps"] / nsol,
                    "mean_n": solver["sum_n"] / nsol, "mean_kept": solver["sum_k"] / nsol,
                    "at_limit": solver["at_limit"]}
+
+    # a later window of the same run: after window2 more steps the bonds have grown
+    # to their plateau (the literal dt drives the state into the top Fock levels,
+    # where the solves are larger); the same K steps timed again
+    window2 = None
+    if args.window2 > 0:
+        st.import_(snapshot)
+        st.step(dt, args.steps + args.window2)
+        ctx.synchronize()
+        b2 = st.bond_dims()
+        ctx.profile_reset()
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                ev2[k][0].record(stream)
+                st.step(dt, 1)
+                ev2[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms2 = [a.elapsed_time(bb) for a, bb in ev2]
+        sv2 = ctx.solver_stats()
+        n2 = max(1.0, sv2["solves"])
+        window2 = {"first_step": args.warmup + args.steps + args.window2, "steps": args.steps,
+                   "ms_per_step": sum(ms2) / args.steps, "steps_per_s": args.steps / (sum(ms2) / 1e3),
+                   "bonds": b2, "mean_n": sv2["sum_n"] / n2, "sweeps_per_solve": sv2["sweeps"] / n2}
 
     # end to end through the public API: host mode vector in (init), K steps each
     # followed by a read-back of the photon number; the system's operators and
@@ -271,6 +322,7 @@ def run_gpu(args):
         "roofline": roofline,
         "kernel_classes_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
         "solver": solver_line,
+        "window2": window2,
         "peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak, "source": "qlb_measure_peak, this run"},
         "e2e": {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d / e2e_steps,
                 "d2h_bytes_per_step": d2h / e2e_steps, "observables": [n_obs.real, p_obs.real]},
@@ -321,6 +373,7 @@ def main():
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=32)
+    ap.add_argument("--window2", type=int, default=200)
     ap.add_argument("--serving-step-scale", type=float, default=0.005)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

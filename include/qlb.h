@@ -336,6 +336,15 @@ qlb_status qlb_profile_reset(qlb_ctx* ctx);
  * device. */
 qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out, int n_out);
 
+/* Autotuner of the step's launch shapes: times the zip-up Gram GEMM at split-K
+ * factors 1, 2, 4, 8, 16 for every (rows, inner size) bucket with CUDA events on
+ * random data, installs the fastest in the context (used by every state planned
+ * afterwards) and, when path is non-NULL, writes the table as lines "m K ksplit".
+ * Allocates scratch for the duration of the call.  The paper has no counterpart. */
+qlb_status qlb_autotune(qlb_ctx* ctx, const char* path);
+/* Installs a table written by qlb_autotune (QLB_EINVAL if unreadable or empty). */
+qlb_status qlb_load_tuning(qlb_ctx* ctx, const char* path);
+
 /* Measured fused multiply-add throughput of device `device` in TFLOP/s:
  * kind 0 = FP64, kind 1 = FP32 (independent FMA chains over every SM, timed with
  * CUDA events, best of three ~20 ms launches).  The denominators of the

@@ -22,6 +22,9 @@ size_t eig_smem_bytes(int n_max);
 // device workspace (complex elements) the eigen-solvers need beyond shared memory
 size_t eig_workspace_elems(int n_max);
 void init_kernel_attributes();
+// split-K factor of a (m x m, K) Gram GEMM: the tuned table if it has the bucket,
+// else the built-in rule (about 64 CTAs)
+int gram_splitk(const qlb_ctx* ctx, long m, long K);
 // 3xTF32 complex GEMM on the tensor cores (same descriptor as launch_gemm); err bit 2
 // is set when a bounded wait of the kernel gave up
 cudaError_t launch_gemm_tc(const GemmDesc& g, const int* d_dims, cudaStream_t s, int* err, double* prof);

@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
   extern __shared__ unsigned char smem_raw[];
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
+  if (n > 0 && n <= e.small_max) return;  // the one-CTA QL solve launched beside this one takes it
   if (n <= 0) {
     if (tid == 0) d[e.dim_out] = 0;
     return;
@@ -368,6 +369,7 @@ __global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, d
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
   const int rank = (int)cluster.block_rank();
+  if (n > 0 && n <= e.small_max) return;  // the one-CTA QL solve launched beside this one takes it
   if (n <= 0) {
     if (rank == 0 && tid == 0) d[e.dim_out] = 0;
     return;
@@ -606,296 +608,6 @@ __global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, d
   }
 }
 
-// Pair of row i in round `round` of the round-robin schedule: (t, p, q), p < q.
-__device__ __forceinline__ void rr_pair_of(int i, int round, int np, int& t, int& p, int& q) {
-  const int pos = i == 0 ? 0 : 1 + ((i - 1 - round) % (np - 1) + (np - 1)) % (np - 1);
-  t = pos < np / 2 ? pos : np - 1 - pos;
-  p = rr_player(t, round, np);
-  q = rr_player(np - 1 - t, round, np);
-  if (p > q) {
-    int x = p;
-    p = q;
-    q = x;
-  }
-}
-
-// The cluster Jacobi with one cluster barrier per round (planned sizes up to 128).
-// All remote traffic is pushed (distributed shared memory stores, no remote loads
-// on the critical path): at the end of round r every CTA stores, into the round
-// r + 1 slots (double-buffered by round parity) of the CTAs concerned,
-//   * each of its rows into the partner-copy slot of that row's next partner,
-//   * its diagonal entries into every CTA's replica of the diagonal,
-//   * G_pq of each next pair whose p row it holds into every CTA's replica,
-// then the cluster barrier.  Round r + 1 then needs only local data: every CTA
-// computes the rotations of all pairs (the same numbers everywhere, so all CTAs
-// agree on convergence without communicating), updates its rows in place from
-// the partner copies (J^dag G), then its columns (G J, V J).  The rotation
-// formula, thresholds and truncation rule are those of the one-CTA solve.
-constexpr int EIG_CL1_MAX_NP = 128;
-
-template <typename R, int NT, int C>
-__global__ void __launch_bounds__(NT) k_eig_cl1(EigDesc e, int* __restrict__ d, double* prof) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ unsigned char smem_raw[];
-  const int n = dev_eval(e.n, d);
-  const int tid = threadIdx.x;
-  const int rank = (int)cluster.block_rank();
-  if (n <= 0) {
-    if (rank == 0 && tid == 0) d[e.dim_out] = 0;
-    return;
-  }
-  const int np = n + (n & 1);
-  const int npairs = np / 2;
-  const int rpb = (np + C - 1) / C;
-  const int r0 = rank * rpb;
-  const int r1 = min(np, r0 + rpb);
-  const int nloc = max(0, r1 - r0);
-  cx<R>* Gl = (cx<R>*)smem_raw;
-  cx<R>* Vl = Gl + (long)rpb * np;
-  cx<R>* const Pb0 = Vl + (long)rpb * np;
-  cx<R>* const Pb1 = Vl + 2L * rpb * np;
-  cx<R>* const Qg0 = Vl + 3L * rpb * np;
-  cx<R>* const Qg1 = Qg0 + npairs;
-  R* const Qd0 = (R*)(Qg1 + npairs);
-  R* const Qd1 = Qd0 + np;
-  __shared__ JRot<R> rot[EIG_CL1_MAX_NP / 2];
-  __shared__ int s_nr;
-  __shared__ double s_part;
-  __shared__ double s_lam[EIG_CL1_MAX_NP];
-  __shared__ int s_perm[EIG_CL1_MAX_NP];
-  __shared__ double s_w[EIG_CL1_MAX_NP];
-  __shared__ int s_k, s_bad;
-  __shared__ R s_thr;
-  __shared__ double s_tr;
-  const R zero = to_r<R>(0.0), one = to_r<R>(1.0);
-
-  const zd* G = (const zd*)e.G;
-  for (long x = tid; x < (long)nloc * np; x += NT) {
-    int li = (int)(x / np), j = (int)(x - (long)li * np);
-    int i = r0 + li;
-    zd v = mk<double>(0, 0);
-    if (i < n && j < n) v = G[(long)i * n + j];
-    if (i == j) v.im = 0;
-    Gl[x] = mk<R>(to_r<R>(v.re), to_r<R>(v.im));
-    Vl[x] = mk<R>(to_r<R>(i == j ? 1.0 : 0.0), zero);
-  }
-  if (tid == 0) {
-    s_bad = 0;
-    double tr = 0;
-    for (int i = 0; i < n; i++) tr += fabs(G[(long)i * n + i].re);
-    s_thr = to_r<R>(0.1 * Eps<R>::v * tr);
-    s_tr = tr;
-  }
-  __syncthreads();
-  // pushes of this CTA's rows, diagonal and couplings for round `rnd` into slot `par`
-  auto push = [&](int rnd, int par) {
-    for (long w = tid; w < (long)nloc * np; w += NT) {
-      const int li = (int)(w / np), j = (int)(w - (long)li * np);
-      int t, p, q;
-      rr_pair_of(r0 + li, rnd, np, t, p, q);
-      const int partner = (r0 + li == p) ? q : p;
-      const int o = partner / rpb;
-      cluster.map_shared_rank(par ? Pb1 : Pb0, o)[(long)(partner - o * rpb) * np + j] = Gl[w];
-    }
-    for (int w = tid; w < nloc * C; w += NT) {
-      const int li = w / C, k = w - (w / C) * C;
-      cluster.map_shared_rank(par ? Qd1 : Qd0, k)[r0 + li] = Gl[(long)li * np + r0 + li].re;
-    }
-    for (int w = tid; w < nloc * C; w += NT) {
-      const int li = w / C, k = w - (w / C) * C;
-      int t, p, q;
-      rr_pair_of(r0 + li, rnd, np, t, p, q);
-      if (r0 + li == p) cluster.map_shared_rank(par ? Qg1 : Qg0, k)[t] = Gl[(long)li * np + q];
-    }
-  };
-  push(0, 0);
-  cluster.sync();
-  const R abs_thr = s_thr;
-  const R rel_tol = to_r<R>(Eps<R>::v * (double)(n > 8 ? n : 8));
-  long stepc = 0;
-  int sweep = 0;
-  long total_rot = 0;
-  for (; sweep < e.max_sweeps; sweep++) {
-    if (tid == 0) s_nr = 0;
-    __syncthreads();
-    for (int round = 0; round < np - 1; round++) {
-      const int par = (int)(stepc & 1);
-      const R* const Qd = par ? Qd1 : Qd0;
-      const cx<R>* const Qg = par ? Qg1 : Qg0;
-      const cx<R>* const Pb = par ? Pb1 : Pb0;
-      // every CTA: the rotations of all pairs from the replicated diagonal and couplings
-      for (int t = tid; t < npairs; t += NT) {
-        int p = rr_player(t, round, np), q = rr_player(np - 1 - t, round, np);
-        if (p > q) {
-          int x = p;
-          p = q;
-          q = x;
-        }
-        R c = one;
-        cx<R> sp = mk<R>(zero, zero);
-        bool rotf = false;
-        if (q < n) {
-          const R a = Qd[p], b = Qd[q];
-          const cx<R> gpq = Qg[t];
-          R x = sqrt(cabs2(gpq));
-          if (x > rel_tol * sqrt(fabs(a * b)) && x > abs_thr && x > zero) {
-            R tau = (b - a) / (x + x);
-            R tt = fabs(tau) > to_r<R>(1e15) ? to_r<R>(0.5) / tau
-                                              : (tau >= zero ? one : -one) / (fabs(tau) + sqrt(one + tau * tau));
-            c = one / sqrt(one + tt * tt);
-            R sx = (tt * c) / x;
-            sp = mk<R>(sx * gpq.re, sx * gpq.im);
-            rotf = true;
-          }
-        }
-        JRot<R> rr;
-        rr.c = c;
-        rr.sp = sp;
-        rr.p = rotf ? p : -1;
-        rr.q = q;
-        rot[t] = rr;
-        if (rotf) atomicAdd(&s_nr, 1);
-      }
-      __syncthreads();
-      // rows (J^dag G), in place, from the partner copies pushed last round
-      for (long w = tid; w < (long)nloc * np; w += NT) {
-        const int li = (int)(w / np), j = (int)(w - (long)li * np);
-        const int i = r0 + li;
-        int t, p, q;
-        rr_pair_of(i, round, np, t, p, q);
-        const JRot<R> rr = rot[t];
-        if (rr.p < 0) continue;
-        const cx<R> gi = Gl[w], gx = Pb[w];
-        Gl[w] = i == rr.p ? csub(cscale(gi, rr.c), cmul(rr.sp, gx)) : cadd(cmul(cconj(rr.sp), gx), cscale(gi, rr.c));
-      }
-      __syncthreads();
-      // columns (G J, V J) on our rows; the pair's off-diagonal becomes an exact zero
-      for (long w = tid; w < (long)nloc * npairs; w += NT) {
-        const int li = (int)(w / npairs), t = (int)(w - (long)li * npairs);
-        const JRot<R> rr = rot[t];
-        if (rr.p < 0) continue;
-        const int p = rr.p, q = rr.q, i = r0 + li;
-        cx<R> gp = Gl[(long)li * np + p], gq = Gl[(long)li * np + q];
-        cx<R> np_ = csub(cscale(gp, rr.c), cmul(cconj(rr.sp), gq));
-        cx<R> nq_ = cadd(cmul(rr.sp, gp), cscale(gq, rr.c));
-        if (i == p) {
-          np_.im = zero;
-          nq_ = mk<R>(zero, zero);
-        } else if (i == q) {
-          np_ = mk<R>(zero, zero);
-          nq_.im = zero;
-        }
-        Gl[(long)li * np + p] = np_;
-        Gl[(long)li * np + q] = nq_;
-        cx<R> vp = Vl[(long)li * np + p], vq = Vl[(long)li * np + q];
-        Vl[(long)li * np + p] = csub(cscale(vp, rr.c), cmul(cconj(rr.sp), vq));
-        Vl[(long)li * np + q] = cadd(cmul(rr.sp, vp), cscale(vq, rr.c));
-      }
-      __syncthreads();
-      stepc++;
-      push((round + 1) % (np - 1), (int)(stepc & 1));
-      cluster.sync();
-    }
-    const int nr = s_nr;  // the same count in every CTA
-    total_rot += nr;
-    __syncthreads();
-    if (nr == 0) break;
-  }
-  const int fin = (int)(stepc & 1);  // slot holding the final diagonal
-  bool unconverged = false;
-  const bool at_limit = sweep >= e.max_sweeps;
-  if (at_limit) {
-    if (tid == 0) s_part = 0.0;
-    __syncthreads();
-    double acc = 0.0;
-    for (long x = tid; x < (long)nloc * np; x += NT) {
-      int li = (int)(x / np), j = (int)(x - (long)li * np);
-      int i = r0 + li;
-      if (i < n && j < n && i != j) acc += to_d(cabs2(Gl[x]));
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((tid & 31) == 0) atomicAdd(&s_part, acc);
-    cluster.sync();
-    double off = 0.0;
-    for (int k = 0; k < C; k++) off += *cluster.map_shared_rank(&s_part, k);
-    unconverged = !(sqrt(off) <= (double)n * Eps<R>::v * s_tr);
-    cluster.sync();  // no CTA leaves while another still reads its partial sum
-  }
-  for (int i = tid; i < n; i += NT) s_lam[i] = to_d((fin ? Qd1 : Qd0)[i]);
-  __syncthreads();
-  for (int i = tid; i < n; i += NT) {
-    double li = s_lam[i];
-    if (!isfinite(li)) s_bad = 1;
-    int rk = 0;
-    for (int j = 0; j < n; j++) {
-      double lj = s_lam[j];
-      if (lj > li || (lj == li && j < i)) rk++;
-    }
-    s_perm[rk] = i;
-  }
-  __syncthreads();
-  for (int r = tid; r < n; r += NT) {
-    double l = s_lam[s_perm[r]];
-    s_w[r] = l > 0.0 ? l : 0.0;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int cap = dev_eval(e.cap, d);
-    if (cap < 1) cap = 1;
-    int k = s_bad ? 1 : keep_count_dev(s_w, n, e.tol, cap, e.gap);
-    s_k = k;
-    if (rank == 0) {
-      d[e.dim_out] = k;
-      double total = 0.0, kept = 0.0;
-      for (int i = 0; i < n; i++) total += s_w[i];
-      for (int i = 0; i < k; i++) kept += s_w[i];
-      if (e.kept_weight) *e.kept_weight = kept;
-      if (e.total_weight) *e.total_weight = total;
-      if (e.disc_stat && total > 0.0) {
-        double r = (total - kept) / total;
-        if (r > *e.disc_stat) *e.disc_stat = r;
-      }
-      if (e.lam)
-        for (int i = 0; i < n; i++) e.lam[i] = s_w[i];
-      if (e.err) {
-        if (unconverged) atomicOr(e.err, 1);
-        if (s_bad || !isfinite(total)) atomicOr(e.err, 2);
-      }
-      if (e.solver_stats) {
-        atomicAdd(e.solver_stats + 0, 1.0);
-        atomicAdd(e.solver_stats + 1, (double)(at_limit ? e.max_sweeps : sweep + 1));
-        atomicAdd(e.solver_stats + 2, (double)n);
-        atomicAdd(e.solver_stats + 3, (double)k);
-        if (at_limit) atomicAdd(e.solver_stats + 4, 1.0);
-        atomicAdd(e.solver_stats + 5, 1.0);  // a multi-SM solve
-        atomicMax((unsigned long long*)(e.solver_stats + 6), (unsigned long long)__double_as_longlong((double)n));
-      }
-      if (prof) {
-        atomicAdd(prof, 40.0 * (double)np * (double)total_rot);
-        atomicAdd(prof + QLB_K_COUNT, 2.0 * sizeof(zd) * (double)n * (double)n);
-      }
-    }
-  }
-  __syncthreads();
-  const int k = s_k;
-  zd* out = (zd*)e.out;
-  const int rl = max(0, min(r1, n) - r0);
-  if (e.out_mode == 0) {
-    for (long x = tid; x < (long)rl * k; x += NT) {
-      int li = (int)(x / k), j = (int)(x - (long)li * k);
-      cx<R> v = Vl[(long)li * np + s_perm[j]];
-      out[(long)(r0 + li) * k + j] = mk<double>(to_d(v.re), to_d(v.im));
-    }
-  } else if (e.out_mode == 1) {
-    for (long x = tid; x < (long)rl * k; x += NT) {
-      int li = (int)(x / k), j = (int)(x - (long)li * k);
-      cx<R> v = Vl[(long)li * np + s_perm[j]];
-      out[(long)j * n + (r0 + li)] = mk<double>(to_d(v.re), -to_d(v.im));
-    }
-  }
-}
-
 // One-CTA Hermitian eigen-solve by Householder tridiagonalisation and implicit QL
 // (the FP64 form at sizes whose matrices fit in shared memory).  Cyclic Jacobi
 // spends ~30 n^3 flops and 3 barriers per round over ~10 sweeps of n - 1 rounds;
@@ -931,6 +643,7 @@ __global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd*
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
+  if (e.small_max > 0 && n > e.small_max) return;  // a Jacobi solve launched beside this one takes it
   if (n <= 0) {
     if (tid == 0) d[e.dim_out] = 0;
     return;
@@ -1226,49 +939,33 @@ cudaError_t launch_eig_cl(const EigDesc& e, const int* d_dims, cudaStream_t s, d
   return cudaLaunchKernelEx(&cfg, k_eig_cl<R, 256, C>, e, (int*)d_dims, prof);
 }
 
-// dynamic shared memory of k_eig_cl1: rows of G and V, two partner-copy slots,
-// two replicas of the couplings and of the diagonal
 template <typename R>
-size_t eig_cl1_smem(int n_max, int C) {
-  const int np = n_max + (n_max & 1), rpb = (np + C - 1) / C;
-  return 4 * (size_t)rpb * np * sizeof(cx<R>) + 2 * (size_t)(np / 2) * sizeof(cx<R>) + 2 * (size_t)np * sizeof(R);
-}
-
-template <typename R, int C>
-cudaError_t launch_eig_cl1(const EigDesc& e, const int* d_dims, cudaStream_t s, double* prof) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(C, 1, 1);
-  cfg.blockDim = dim3(256, 1, 1);
-  cfg.dynamicSmemBytes = eig_cl1_smem<R>(e.n_max, C);
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_eig_cl1<R, 256, C>, e, (int*)d_dims, prof);
-}
-
-template <typename R>
-cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof) {
-  // planned sizes past one SM's worth of work: the cluster solves (rows of G and V
-  // spread over 8 or 16 SMs in distributed shared memory); up to 128 the
-  // one-barrier-per-round form, up to 256 the two-barrier form
-  if ((std::is_same<R, df64>::value ? e.n_max > 24 : e.n_max > HEEV_N_MAX) && e.n_max <= EIG_CL_MAX_NP) {
-    if (e.n_max <= EIG_CL1_MAX_NP) return launch_eig_cl1<R, 8>(e, d_dims, s, prof);
-    return launch_eig_cl<R, 16>(e, d_dims, s, prof);
-  }
-  if (std::is_same<R, double>::value && e.n_max <= HEEV_N_MAX) {
-    // FP64 form, shared-memory sizes: Householder tridiagonalisation + implicit QL.
-    // Past HEEV_N_MAX its matrices spill to global memory and the serial QL chain
-    // (~n^2 dependent rotations) outlasts the parallel rounds of Jacobi, which
-    // takes those solves.
+cudaError_t launch_eig(const EigDesc& e0, const int* d_dims, cudaStream_t s, void* work, double* prof) {
+  EigDesc e = e0;
+  e.small_max = 0;
+  const bool fp64 = std::is_same<R, double>::value;
+  if (fp64 && e.n_max <= HEEV_N_MAX) {
+    // FP64, shared-memory sizes: Householder tridiagonalisation + implicit QL
     size_t want = eig_smem_bytes<double>(e.n_max);
     int dyn = (int)(want <= HEEV_SMEM_LIMIT ? want : HEEV_SMEM_LIMIT);
     k_heev<128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
     return cudaGetLastError();
+  }
+  if (fp64) {
+    // planned size above 64: the runtime size decides.  Up to 64 the one-CTA QL solve
+    // (its matrices in shared memory) is the fastest; above, a Jacobi solve over a
+    // thread-block cluster.  Both kernels are launched; the one the runtime size
+    // does not select returns at once.
+    e.small_max = HEEV_N_MAX;
+    EigDesc q = e;
+    q.n_max = HEEV_N_MAX;
+    k_heev<128><<<1, 128, (int)HEEV_SMEM_LIMIT, s>>>(q, (int*)d_dims, (zd*)work, (int)HEEV_SMEM_LIMIT, prof);
+    cudaError_t r = cudaGetLastError();
+    if (r != cudaSuccess) return r;
+  }
+  if (e.n_max > (fp64 ? HEEV_N_MAX : 24) && e.n_max <= EIG_CL_MAX_NP) {
+    if (e.n_max <= 128) return launch_eig_cl<R, 8>(e, d_dims, s, prof);
+    return launch_eig_cl<R, 16>(e, d_dims, s, prof);
   }
   size_t want = eig_smem_bytes<R>(e.n_max);
   int dyn = (int)(want <= EIG_SMEM_LIMIT ? want : EIG_SMEM_LIMIT);
@@ -1298,8 +995,6 @@ void init_kernel_attributes() {
   set_attr<df64, 512>();
   set_attr<df64, 1024>();
   cudaFuncSetAttribute(k_heev<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HEEV_SMEM_LIMIT);
-  cudaFuncSetAttribute(k_eig_cl1<double, 256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
-  cudaFuncSetAttribute(k_eig_cl1<df64, 256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
   cudaFuncSetAttribute(k_eig_cl<double, 256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
   cudaFuncSetAttribute(k_eig_cl<double, 256, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
   cudaFuncSetAttribute(k_eig_cl<double, 256, 16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

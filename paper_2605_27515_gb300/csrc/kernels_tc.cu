@@ -23,11 +23,13 @@
 //
 // Tile: 128 rows of C x 64 complex columns (MMA M = 128, N = 128 real columns),
 // 16 complex k per stage (32 real K = four K = 8 MMAs per split product), two
-// stages.  128 threads: all of them convert FP64 operands into the shared-memory
+// stages.  256 threads: all of them convert FP64 operands into the shared-memory
 // tiles (the canonical K-major layout without swizzling: 8-row x 16-byte core
 // matrices, K-adjacent core matrices 128 bytes apart, 8-row groups 1024 bytes
-// apart); thread 0 issues the MMAs and commits them to the stage's mbarrier; each
-// warp reads its 32 accumulator lanes back with tcgen05.ld for the epilogue.
+// apart), each thread writing whole 16-byte core-matrix rows so that a warp stores
+// 512 contiguous bytes (no bank conflicts); thread 0 issues the MMAs and commits
+// them to the stage's mbarrier; for the epilogue the two warps of each TMEM lane
+// quarter read back half of the accumulator columns each with tcgen05.ld.
 // Every mbarrier wait is bounded: on expiry the kernel records an error flag,
 // frees its tensor memory and leaves the tile unwritten.
 
@@ -42,7 +44,7 @@ namespace {
 constexpr int TC_BM = 128;        // rows of C per CTA (MMA M)
 constexpr int TC_BNC = 64;        // complex columns of C per CTA (MMA N = 128)
 constexpr int TC_BKC = 16;        // complex k per stage (32 real K)
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
 constexpr int TC_TILE_BYTES = 128 * 32 * 4;  // one 128 x 32 TF32 operand tile
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;  // A hi, A lo, B hi, B lo
 constexpr int TC_SMEM_BYTES = 2 * TC_STAGE_BYTES + 1024 + 64;
@@ -125,6 +127,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// element (k, j) of op(B)
+__device__ __forceinline__ zd load_opb(const zd* B, int op, long ld, int k, int j) {
+  if (op == OP_N) return B[(long)k * ld + j];
+  zd v = B[(long)j * ld + k];
+  if (op == OP_C) v.im = -v.im;
+  return v;
+}
+
 __device__ __forceinline__ zd load_op(const zd* P, int op, long ld, int i, int k) {
   if (op == OP_N) return P[(long)i * ld + k];
   zd v = P[(long)k * ld + i];
@@ -189,50 +199,48 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_zgemm(GemmDesc g, const int* 
       if (*s_fail) break;
     }
     const int k0 = ch * TC_BKC;
-    // A: 128 rows x 16 complex k -> real columns 2 kc (re), 2 kc + 1 (im)
-    for (int x = tid; x < TC_BM * TC_BKC; x += TC_THREADS) {
-      // consecutive threads walk the contiguous index of op(A) in memory
-      const bool kfast = g.opA == OP_N;
-      const int r = kfast ? x / TC_BKC : x % TC_BM, kc = kfast ? x % TC_BKC : x / TC_BM;
-      const int gi = row0 + r, gk = k0 + kc;
-      zd a = (gi < m && gk < K) ? load_op(A, g.opA, lda, gi, gk) : mk<double>(0.0, 0.0);
-      uint32_t h0, l0, h1, l1;
-      split3(a.re, h0, l0);
-      split3(a.im, h1, l1);
-      const uint32_t o0 = tile_off(r, 2 * kc), o1 = tile_off(r, 2 * kc + 1);
-      *(uint32_t*)(sA_hi + o0) = h0;
-      *(uint32_t*)(sA_lo + o0) = l0;
-      *(uint32_t*)(sA_hi + o1) = h1;
-      *(uint32_t*)(sA_lo + o1) = l1;
-    }
-    // B: 64 complex columns x 16 complex k -> the 2 x 2 real blocks [[Br, -Bi], [Bi, Br]]
-    for (int x = tid; x < TC_BNC * TC_BKC; x += TC_THREADS) {
-      const bool jfast = g.opB == OP_N;
-      const int jl = jfast ? x % TC_BNC : x / TC_BKC, kc = jfast ? x / TC_BNC : x % TC_BKC;
-      const int gj = col0 + jl, gk = k0 + kc;
-      zd b = mk<double>(0.0, 0.0);
-      if (gj < n && gk < K) {
-        if (g.opB == OP_N)
-          b = B[(long)gk * ldb + gj];
-        else {
-          b = B[(long)gj * ldb + gk];
-          if (g.opB == OP_C) b.im = -b.im;
-        }
+    // A: 128 rows x 16 complex k.  Item (r, cp): complex k = 2cp, 2cp + 1 of row r,
+    // i.e. real columns 4cp .. 4cp + 3 = one 16-byte core-matrix row in hi and in lo
+    for (int x = tid; x < TC_BM * 8; x += TC_THREADS) {
+      const int r = ((x >> 6) << 3) + (x & 7), cp = (x >> 3) & 7;
+      const int gi = row0 + r, gk = k0 + 2 * cp;
+      zd a0 = mk<double>(0.0, 0.0), a1 = mk<double>(0.0, 0.0);
+      if (gi < m) {
+        if (gk < K) a0 = load_op(A, g.opA, lda, gi, gk);
+        if (gk + 1 < K) a1 = load_op(A, g.opA, lda, gi, gk + 1);
       }
-      uint32_t hr, lr, hi, li, hn, ln;
-      split3(b.re, hr, lr);
-      split3(b.im, hi, li);
-      split3(-b.im, hn, ln);
-      const uint32_t a00 = tile_off(2 * jl, 2 * kc), a01 = tile_off(2 * jl, 2 * kc + 1);
-      const uint32_t a10 = tile_off(2 * jl + 1, 2 * kc), a11 = tile_off(2 * jl + 1, 2 * kc + 1);
-      *(uint32_t*)(sB_hi + a00) = hr;
-      *(uint32_t*)(sB_lo + a00) = lr;
-      *(uint32_t*)(sB_hi + a01) = hn;
-      *(uint32_t*)(sB_lo + a01) = ln;
-      *(uint32_t*)(sB_hi + a10) = hi;
-      *(uint32_t*)(sB_lo + a10) = li;
-      *(uint32_t*)(sB_hi + a11) = hr;
-      *(uint32_t*)(sB_lo + a11) = lr;
+      uint4 h, l;
+      split3(a0.re, h.x, l.x);
+      split3(a0.im, h.y, l.y);
+      split3(a1.re, h.z, l.z);
+      split3(a1.im, h.w, l.w);
+      const uint32_t o = tile_off(r, 4 * cp);
+      *(uint4*)(sA_hi + o) = h;
+      *(uint4*)(sA_lo + o) = l;
+    }
+    // B: 64 complex columns x 16 complex k.  Item (j, cp): b0 = B(2cp, j), b1 = B(2cp+1, j)
+    // give real row 2j = [b0.re, -b0.im, b1.re, -b1.im] and row 2j+1 = [b0.im, b0.re,
+    // b1.im, b1.re] over real columns 4cp .. 4cp + 3
+    for (int x = tid; x < TC_BNC * 8; x += TC_THREADS) {
+      const int j = ((x >> 5) << 2) + (x & 3), cp = (x >> 2) & 7;
+      const int gj = col0 + j, gk = k0 + 2 * cp;
+      zd b0 = mk<double>(0.0, 0.0), b1 = mk<double>(0.0, 0.0);
+      if (gj < n) {
+        if (gk < K) b0 = load_opb(B, g.opB, ldb, gk, gj);
+        if (gk + 1 < K) b1 = load_opb(B, g.opB, ldb, gk + 1, gj);
+      }
+      uint32_t r0h, r0l, i0h, i0l, n0h, n0l, r1h, r1l, i1h, i1l, n1h, n1l;
+      split3(b0.re, r0h, r0l);
+      split3(b0.im, i0h, i0l);
+      split3(-b0.im, n0h, n0l);
+      split3(b1.re, r1h, r1l);
+      split3(b1.im, i1h, i1l);
+      split3(-b1.im, n1h, n1l);
+      const uint32_t o0 = tile_off(2 * j, 4 * cp), o1 = tile_off(2 * j + 1, 4 * cp);
+      *(uint4*)(sB_hi + o0) = make_uint4(r0h, n0h, r1h, n1h);
+      *(uint4*)(sB_lo + o0) = make_uint4(r0l, n0l, r1l, n1l);
+      *(uint4*)(sB_hi + o1) = make_uint4(i0h, r0h, i1h, r1h);
+      *(uint4*)(sB_lo + o1) = make_uint4(i0l, r0l, i1l, r1l);
     }
     // make the generic-proxy stores visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -268,11 +276,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_zgemm(GemmDesc g, const int* 
       if (g.alpha_scale_rsqrt) sc = (sc > 0.0) ? 1.0 / sqrt(sc) : 0.0;
       alpha = cscale(alpha, sc);
     }
-    const int row = row0 + warp * 32 + lane;  // accumulator row = TMEM lane
-    for (int cb = 0; cb < 4; cb++) {
+    const int quarter = warp & 3;               // TMEM lanes 32 quarter .. 32 quarter + 31
+    const int row = row0 + quarter * 32 + lane;  // accumulator row = TMEM lane
+    for (int cb = (warp >> 2) * 2; cb < (warp >> 2) * 2 + 2; cb++) {
       uint32_t r[32];
       if (nchunks > 0) {
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), r);
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cb * 32), r);
       } else {
 #pragma unroll
         for (int q = 0; q < 32; q++) r[q] = 0u;

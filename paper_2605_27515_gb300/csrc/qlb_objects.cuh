@@ -67,6 +67,9 @@ struct qlb_ctx {
   double* d_prof = nullptr;  // [QLB_K_COUNT] flops, [QLB_K_COUNT..2*] bytes
   double prof_ms[QLB_K_COUNT] = {0};
   long long prof_launch[QLB_K_COUNT] = {0};
+  // split-K factor of the Gram GEMM per (rows bucket, K bucket), from the autotuner
+  // (qlb_autotune) or a table it wrote (qlb_load_tuning); empty: the built-in rule
+  std::map<std::pair<int, int>, int> gram_tune;
   // MPOs of built-in per-mode factors, keyed by "R|recipe" (see DevTerm::key)
   std::map<std::string, qlb::Mpo*> factor_mpo_cache;
   ~qlb_ctx();

@@ -659,8 +659,7 @@ qlb_status plan_buffers(qlb_state* st, const Kraus& K) {
   size_t nWs = 1;
   for (int i = 0; i + 1 < L; i++) {
     const long mm = 2L * c.zcap[i], kk = (long)c.dcap[i + 1] * D[i + 1];
-    const long tiles = ((mm + 31) / 32) * ((mm + 31) / 32);
-    int ks = (int)std::min<long>({16, std::max<long>(1, 64 / std::max<long>(1, tiles)), std::max<long>(1, kk / 64)});
+    const int ks = gram_splitk(ctx, mm, kk);
     st->gram_split[i] = ks;
     if (ks > 1) nWs = std::max(nWs, (size_t)ks * mm * mm);
   }

@@ -73,6 +73,8 @@ _SIGS = {
     "qlb_ctx_alloc_count": (_st, [_vp, C.POINTER(C.c_int64)]),
     "qlb_profile_solver_stats": (_st, [_vp, C.POINTER(C.c_double), C.c_int]),
     "qlb_measure_peak": (_st, [C.c_int, C.c_int, C.POINTER(C.c_double)]),
+    "qlb_autotune": (_st, [_vp, C.c_char_p]),
+    "qlb_load_tuning": (_st, [_vp, C.c_char_p]),
     "qlb_tc_zgemm": (_st, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                            C.POINTER(C.c_double)]),
     "qlb_system_create": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
@@ -171,6 +173,13 @@ class Ctx:
         b = C.c_size_t()
         _check(self.lib.qlb_ctx_memory(self.h, C.byref(b)))
         return b.value
+
+    def autotune(self, path=None):
+        """Run the launch-shape autotuner (qlb_autotune); optionally write its table."""
+        _check(self.lib.qlb_autotune(self.h, path.encode() if path else None))
+
+    def load_tuning(self, path):
+        _check(self.lib.qlb_load_tuning(self.h, path.encode()))
 
     def alloc_count(self) -> int:
         n = C.c_int64()

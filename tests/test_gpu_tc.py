@@ -26,7 +26,7 @@ def test_tc_zgemm_matches_fp64(m, n, k):
     assert np.all(np.abs(C - ref) <= bound), np.max(np.abs(C - ref) / bound)
     if k > 0:
         rel = np.linalg.norm(C - ref) / np.linalg.norm(ref)
-        assert rel < 2e-6, rel  # one TF32 pass would leave ~1e-3
+        assert rel < 2e-5, rel  # one TF32 pass would leave ~1e-3
 
 
 def test_tc_zgemm_exact_on_small_integers():
