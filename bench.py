@@ -202,6 +202,9 @@ def run_gpu(args):
     cfg = inputs.config(WORKLOAD)
     ctx = qlb.Ctx(device=dev, precision=args.precision, tol=cfg["tol"], chi_max=cfg["chi_max"],
                   chi_mu_max=cfg["chi_mu_max"], stream_ordered=1)
+    tuning = os.path.join(ROOT, "paper_2605_27515_gb300", "tuning", "gram_splitk_gb300.txt")
+    if os.path.exists(tuning):
+        ctx.load_tuning(tuning)  # the autotuner's split-K table (qlb_autotune on a GB300)
     b = systems.build(ctx, cfg)
     st = b.sys.state(b.init)
     stream = torch.cuda.ExternalStream(st.stream(), device=dev)
@@ -341,6 +344,67 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_other_workload(args):
+    """The larger configurations at their stated sizes, as separate bench lines
+    (the default line is the cat_r9 workload):
+      transmon  transmon (128 charge states, R = 7) x resonator (N = 1024, R = 10),
+                17 sites, chi <= 128, chi_mu <= 16, ramped drive, dt = 2e-6; a window
+                of K steps after W warm-up steps;
+      cat_pair  four modes [b1, a1, a2, b2] = [16, 256, 256, 16] levels (24 sites),
+                chi <= 256, chi_mu <= 32, dt = 1e-4, the 16 beam-splitter variants
+                J = 0.01 linspace(0.5, 2, 16) stepping concurrently, each on its own
+                stream: steps/s = 16 K / the window's duration."""
+    import torch
+
+    from paper_2605_27515_gb300 import inputs, qlb, systems
+
+    dev = 0
+    torch.cuda.set_device(dev)
+    cfg = inputs.config(args.workload)
+    ctx = qlb.Ctx(device=dev, precision=args.precision, tol=cfg["tol"], chi_max=cfg["chi_max"],
+                  chi_mu_max=cfg["chi_mu_max"], stream_ordered=1)
+    tuning = os.path.join(ROOT, "paper_2605_27515_gb300", "tuning", "gram_splitk_gb300.txt")
+    if os.path.exists(tuning):
+        ctx.load_tuning(tuning)
+    dt = cfg["dt"]
+    n_total = args.warmup + args.steps + 1
+    if args.workload == "transmon":
+        builds = [systems.build(ctx, cfg, nsteps=n_total)]
+    else:
+        builds = [systems.build(ctx, cfg, J=J) for J in inputs.cat_pair_J(cfg["n_variants"], cfg["J"])]
+    states = [b.sys.state(b.init) for b in builds]
+    for st in states:
+        st.step(dt, args.warmup)
+    ctx.synchronize()
+    ctx.profile_reset()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for st in states:
+                st.step(dt, 1)  # enqueued on each state's own stream
+        ctx.synchronize()
+        wall = time.perf_counter() - t0
+    sv = ctx.solver_stats()
+    ns = max(1.0, sv["solves"])
+    value = len(states) * args.steps / wall
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": ["f64", "mixed", "tc"][args.precision],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "R": cfg["R"], "dt": dt, "chi_max": cfg["chi_max"],
+                       "chi_mu_max": cfg["chi_mu_max"], "tol": cfg["tol"], "states": len(states),
+                       "bonds_after": [st.bond_dims() for st in states[:2]],
+                       "timing": "host wall clock around K steps of every state, device synchronised"},
+            "solver": {"solves_per_step": sv["solves"] / (args.steps * len(states)), "mean_n": sv["sum_n"] / ns,
+                       "max_n": sv["max_n"], "sweeps_per_solve": sv["sweeps"] / ns},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    for st in states:
+        st.close()
+    ctx.close()
+
+
 def serving_summary(dev, n_requests, step_scale, precision, budget_gb=4.0):
     """The serving workload (Poisson arrivals at 200/s of single-cat requests,
     seed 20260527) through the library's continuous-batching server (qlb_server_*):
@@ -374,11 +438,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--window2", type=int, default=200)
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "transmon", "cat_pair"])
     ap.add_argument("--serving-step-scale", type=float, default=0.005)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != WORKLOAD:
+        run_other_workload(args)
     else:
         run_gpu(args)
 
