@@ -187,20 +187,17 @@ def cpu_baseline_sample():
             "sample": f"{n} dense FP64 Kraus steps of the N=512 cat (about {dt:.0f} s of host time)"}
 
 
-def run_gpu(args):
+def _measure_form(args, dev, precision, world, flush):
+    """One precision form of the cat_r9 workload: W warm-up steps, K timed steps
+    (CUDA events on the state's stream, L2 flushed between steps), a replay of the
+    same K steps from a snapshot with events around every launch (kernel classes and
+    roofline), a later window, and the end-to-end run through the public API."""
     import torch
 
     from paper_2605_27515_gb300 import inputs, qlb, systems
 
-    rank, world, local = dist_info()
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    dev = local
-    torch.cuda.set_device(dev)
     cfg = inputs.config(WORKLOAD)
-    ctx = qlb.Ctx(device=dev, precision=args.precision, tol=cfg["tol"], chi_max=cfg["chi_max"],
+    ctx = qlb.Ctx(device=dev, precision=precision, tol=cfg["tol"], chi_max=cfg["chi_max"],
                   chi_mu_max=cfg["chi_mu_max"], stream_ordered=1)
     tuning = os.path.join(ROOT, "paper_2605_27515_gb300", "tuning", "gram_splitk_gb300.txt")
     if os.path.exists(tuning):
@@ -208,7 +205,6 @@ def run_gpu(args):
     b = systems.build(ctx, cfg)
     st = b.sys.state(b.init)
     stream = torch.cuda.ExternalStream(st.stream(), device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
     dt = cfg["dt"]
     status = st.step(dt, args.warmup)
     ctx.synchronize()
@@ -217,6 +213,8 @@ def run_gpu(args):
     ctx.profile_reset()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
+        import torch.distributed as dist
+
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
@@ -234,6 +232,7 @@ def run_gpu(args):
     ms = [a.elapsed_time(bb) for a, bb in evs]
     value, total_ms = replica_throughput(float(sum(ms)), args.steps, device=f"cuda:{dev}")
     bonds_after = st.bond_dims()
+    obs_end = [st.expectation(b.observables["n"]).real, st.expectation(b.observables["parity"]).real]
     solver = ctx.solver_stats()  # counters of the timed (graph-launched) steps
 
     # kernel-class breakdown of the same steps: the state is put back to the
@@ -252,15 +251,15 @@ def run_gpu(args):
     dp = prof[dom]
     fp64_peak = qlb.qlb_measure_peak(dev, 0)
     fp32_peak = qlb.qlb_measure_peak(dev, 1)
-    # the FP64 form runs the truncation solves on the FP64 pipe; the mixed form runs
-    # them in double-float on the FP32 pipe (its flops are counted in FP64 terms)
-    peak = fp64_peak if args.precision == 0 or dom != "eig" else fp32_peak
     achieved = dp["flops"] / (dp["ms"] / 1e3) / 1e12 if dp["ms"] > 0 else 0.0
     traffic, traffic_src = _traffic(dom)
-    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
-                "peak_source": ("measured FP64 FMA throughput of this GPU (qlb_measure_peak)"
-                                if peak == fp64_peak else "measured FP32 FMA throughput of this GPU"),
+    # the truncation solves do FP64-accurate work: their device-counted flops are set
+    # against the measured FP64 peak in both forms (the double-float form runs them
+    # on the FP32 pipes, each FP64-equivalent operation costing ~10-20 FP32 ones)
+    roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": traffic, "traffic_source": traffic_src,
+                "peak_source": "measured FP64 FMA throughput of this GPU (qlb_measure_peak), of measured",
+                "frac_of_fp32_peak": achieved / fp32_peak,
                 "launches": dp["launches"], "ms_per_launch": dp["ms"] / max(1, dp["launches"]),
                 "flops_per_launch": dp["flops"] / max(1, dp["launches"]),
                 "class_ms_per_step": dp["ms"] / args.steps, "step_ms": total_ms / args.steps,
@@ -309,37 +308,80 @@ def run_gpu(args):
     p_obs = st2.expectation(b.observables["parity"])
     e2e_s = time.perf_counter() - t0
     e2e_steps = args.warmup + args.steps
-    h2d = 16 * 512
-    d2h = 16 * (e2e_steps + 1)
     st2.close()
+    out = {"value": value, "total_ms": total_ms, "status": int(status), "bonds_before": bonds_before,
+           "bonds_after": bonds_after, "obs_end": obs_end, "roofline": roofline,
+           "classes": {k: v["ms"] / args.steps for k, v in prof.items()}, "solver": solver_line,
+           "window2": window2, "peaks": {"fp64": fp64_peak, "fp32": fp32_peak},
+           "e2e": {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 16 * 512 / e2e_steps,
+                   "d2h_bytes_per_step": 16 * (e2e_steps + 1) / e2e_steps, "observables": [n_obs.real, p_obs.real]},
+           "gpu_launches": int(round(launches_per_step * args.steps)), "clocks": clk.summary(), "dt": dt}
+    st.close()
+    ctx.close()
+    return out
 
+
+FORM_DTYPE = {0: "f64", 1: "f64+df64", 2: "f64+df64+tf32x3"}
+FORM_NAME = {0: "fp64", 1: "mixed (double-float eigen-solves)", 2: "tensor-core (3xTF32 MPO application)"}
+
+
+def run_gpu(args):
+    """The headline line.  By default both the plain FP64 form and the mixed form
+    (double-float truncation solves on the FP32 pipes) are measured on the same
+    workload; the line reports the faster one whose photon number and parity at the
+    end of the timed window are within 1e-6 of the FP64 form's (the metric's
+    "steps/s at <= 1e-6 observable error vs the plain FP64 form"), with both forms
+    listed under "forms".  --precision k measures form k alone."""
+    import torch
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    forms = [0, 1] if args.precision < 0 else [args.precision]
+    res = {p: _measure_form(args, dev, p, world, flush) for p in forms}
+    head = forms[0]
+    ref = res.get(0)
+    errs = {}
+    for p in forms:
+        if ref is not None and p != 0:
+            errs[p] = max(abs(a - c) for a, c in zip(res[p]["obs_end"], ref["obs_end"]))
+            if errs[p] <= 1e-6 and res[p]["value"] > res[head]["value"]:
+                head = p
+    r = res[head]
     line = {
-        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "mixed",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": 512, "R": 9, "alpha2": 32.0, "eps_z": 0.1, "dt": dt, "chi_max": 64,
-                   "chi_mu_max": 16, "tol": 1e-12, "l2": "flushed (256 MiB write) between timed steps",
-                   "parallelism": "replicas" if world > 1 else "single", "bonds_before": bonds_before,
-                   "bonds_after": bonds_after, "step_status": int(status)},
-        "roofline": roofline,
-        "kernel_classes_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
-        "solver": solver_line,
-        "window2": window2,
-        "peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak, "source": "qlb_measure_peak, this run"},
-        "e2e": {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d / e2e_steps,
-                "d2h_bytes_per_step": d2h / e2e_steps, "observables": [n_obs.real, p_obs.real]},
-        "gpu_launches": int(round(launches_per_step * args.steps)),
-        "clocks": clk.summary(),
+        "metric": METRIC, "value": r["value"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPE[head], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": 512, "R": 9, "alpha2": 32.0, "eps_z": 0.1, "dt": r["dt"],
+                   "chi_max": 64, "chi_mu_max": 16, "tol": 1e-12, "form": FORM_NAME[head],
+                   "l2": "flushed (256 MiB write) between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single", "bonds_before": r["bonds_before"],
+                   "bonds_after": r["bonds_after"], "step_status": r["status"]},
+        "roofline": r["roofline"],
+        "kernel_classes_ms_per_step": r["classes"],
+        "solver": r["solver"],
+        "window2": r["window2"],
+        "peaks_tflops": dict(r["peaks"], source="qlb_measure_peak, this run"),
+        "e2e": r["e2e"],
+        "gpu_launches": r["gpu_launches"],
+        "clocks": r["clocks"],
+        "forms": {FORM_DTYPE[p]: {"value": res[p]["value"], "ms_per_step": res[p]["total_ms"] / args.steps,
+                                  "e2e": res[p]["e2e"]["value"], "obs_end": res[p]["obs_end"],
+                                  "obs_err_vs_f64": errs.get(p, 0.0 if p == 0 else None),
+                                  "window2_ms_per_step": (res[p]["window2"] or {}).get("ms_per_step"),
+                                  "eig_ms_per_step": res[p]["classes"]["eig"]} for p in forms},
     }
     if args.serving_requests > 0:
-        line["serving"] = serving_summary(dev, args.serving_requests, args.serving_step_scale, args.precision)
+        line["serving"] = serving_summary(dev, args.serving_requests, args.serving_step_scale, max(head, 0))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    st.close()
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -361,7 +403,7 @@ def run_other_workload(args):
     dev = 0
     torch.cuda.set_device(dev)
     cfg = inputs.config(args.workload)
-    ctx = qlb.Ctx(device=dev, precision=args.precision, tol=cfg["tol"], chi_max=cfg["chi_max"],
+    ctx = qlb.Ctx(device=dev, precision=max(args.precision, 0), tol=cfg["tol"], chi_max=cfg["chi_max"],
                   chi_mu_max=cfg["chi_mu_max"], stream_ordered=1)
     tuning = os.path.join(ROOT, "paper_2605_27515_gb300", "tuning", "gram_splitk_gb300.txt")
     if os.path.exists(tuning):
@@ -390,7 +432,7 @@ def run_other_workload(args):
     value = len(states) * args.steps / wall
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": ["f64", "mixed", "tc"][args.precision],
+            "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPE[max(args.precision, 0)],
             "data": "synthetic",
             "config": {"workload": args.workload, "R": cfg["R"], "dt": dt, "chi_max": cfg["chi_max"],
                        "chi_mu_max": cfg["chi_mu_max"], "tol": cfg["tol"], "states": len(states),
@@ -434,7 +476,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=-1,
+                    help="0 FP64, 1 mixed, 2 tensor-core; default: FP64 and mixed, headline the faster within 1e-6")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--window2", type=int, default=200)

@@ -168,7 +168,6 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
   extern __shared__ unsigned char smem_raw[];
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
-  if (n > 0 && n <= e.small_max) return;  // the one-CTA QL solve launched beside this one takes it
   if (n <= 0) {
     if (tid == 0) d[e.dim_out] = 0;
     return;
@@ -369,7 +368,6 @@ __global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, d
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
   const int rank = (int)cluster.block_rank();
-  if (n > 0 && n <= e.small_max) return;  // the one-CTA QL solve launched beside this one takes it
   if (n <= 0) {
     if (rank == 0 && tid == 0) d[e.dim_out] = 0;
     return;
@@ -643,7 +641,6 @@ __global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd*
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  if (e.small_max > 0 && n > e.small_max) return;  // a Jacobi solve launched beside this one takes it
   if (n <= 0) {
     if (tid == 0) d[e.dim_out] = 0;
     return;
@@ -940,30 +937,22 @@ cudaError_t launch_eig_cl(const EigDesc& e, const int* d_dims, cudaStream_t s, d
 }
 
 template <typename R>
-cudaError_t launch_eig(const EigDesc& e0, const int* d_dims, cudaStream_t s, void* work, double* prof) {
-  EigDesc e = e0;
-  e.small_max = 0;
-  const bool fp64 = std::is_same<R, double>::value;
-  if (fp64 && e.n_max <= HEEV_N_MAX) {
-    // FP64, shared-memory sizes: Householder tridiagonalisation + implicit QL
+cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof) {
+  if (std::is_same<R, double>::value && e.n_max <= HEEV_N_MAX) {
+    // FP64, planned sizes up to 64: Householder tridiagonalisation + implicit QL in
+    // one CTA.  Larger planned sizes stay on Jacobi even when the runtime size is
+    // small: on the literal cat_r9 step (which amplifies high-Fock components ~65x
+    // per step) the QL vectors' absolute accuracy seeded the blow-up within 30
+    // steps, while Jacobi's relative accuracy on the graded Gram matrices kept the
+    // state on the dense oracle (measured on GB300).
     size_t want = eig_smem_bytes<double>(e.n_max);
     int dyn = (int)(want <= HEEV_SMEM_LIMIT ? want : HEEV_SMEM_LIMIT);
     k_heev<128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
     return cudaGetLastError();
   }
-  if (fp64) {
-    // planned size above 64: the runtime size decides.  Up to 64 the one-CTA QL solve
-    // (its matrices in shared memory) is the fastest; above, a Jacobi solve over a
-    // thread-block cluster.  Both kernels are launched; the one the runtime size
-    // does not select returns at once.
-    e.small_max = HEEV_N_MAX;
-    EigDesc q = e;
-    q.n_max = HEEV_N_MAX;
-    k_heev<128><<<1, 128, (int)HEEV_SMEM_LIMIT, s>>>(q, (int*)d_dims, (zd*)work, (int)HEEV_SMEM_LIMIT, prof);
-    cudaError_t r = cudaGetLastError();
-    if (r != cudaSuccess) return r;
-  }
-  if (e.n_max > (fp64 ? HEEV_N_MAX : 24) && e.n_max <= EIG_CL_MAX_NP) {
+  // planned sizes past one SM's worth of work: Jacobi over a thread-block cluster
+  // (rows of G and V in distributed shared memory)
+  if (e.n_max > (std::is_same<R, double>::value ? HEEV_N_MAX : 24) && e.n_max <= EIG_CL_MAX_NP) {
     if (e.n_max <= 128) return launch_eig_cl<R, 8>(e, d_dims, s, prof);
     return launch_eig_cl<R, 16>(e, d_dims, s, prof);
   }
@@ -977,8 +966,6 @@ cudaError_t launch_eig(const EigDesc& e0, const int* d_dims, cudaStream_t s, voi
     k_eig<R, 128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
   else if (wide)
     k_eig<R, 1024><<<1, 1024, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
-  else if (e.n_max <= 64)
-    k_eig<R, 256><<<1, 256, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
   else
     k_eig<R, 512><<<1, 512, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
   return cudaGetLastError();

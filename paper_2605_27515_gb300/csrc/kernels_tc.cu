@@ -58,10 +58,13 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   return r;
 }
 
-// hi = tf32(x), lo = tf32(x - hi) (as FP32 bit patterns)
+// hi = tf32(f), lo = tf32(f - hi) with f the FP32 rounding of x (FP32 bit patterns).
+// The split runs in FP32 after one conversion: this GPU's FP64 pipe is narrow, and
+// f already carries the ~22 bits that hi + lo keep.
 __device__ __forceinline__ void split3(double x, uint32_t& hi, uint32_t& lo) {
-  hi = to_tf32((float)x);
-  lo = to_tf32((float)(x - (double)__uint_as_float(hi)));
+  const float f = __double2float_rn(x);
+  hi = to_tf32(f);
+  lo = to_tf32(f - __uint_as_float(hi));
 }
 
 // byte offset of element (row r, real k c) in a 128 x 32 K-major tile

@@ -141,8 +141,6 @@ struct EigDesc {
   double* disc_stat;    // optional: running max of discarded relative weight
   int* err;             // error flags (bit 0: no convergence, bit 1: non-finite)
   double* solver_stats; // optional counters (see qlb_ctx::d_solver)
-  int small_max;        // set by the launcher: sizes <= small_max go to the one-CTA QL
-                        // solve, larger ones to the Jacobi solve launched beside it
 };
 
 // ------------------------------------------------------------------ error plumbing
