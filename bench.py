@@ -198,7 +198,7 @@ def _measure_form(args, dev, precision, world, flush):
 
     cfg = inputs.config(WORKLOAD)
     ctx = qlb.Ctx(device=dev, precision=precision, tol=cfg["tol"], chi_max=cfg["chi_max"],
-                  chi_mu_max=cfg["chi_mu_max"], stream_ordered=1)
+                  chi_mu_max=cfg["chi_mu_max"], stream_ordered=1, mixed_gemm=args.mixed_gemm)
     tuning = os.path.join(ROOT, "paper_2605_27515_gb300", "tuning", "gram_splitk_gb300.txt")
     if os.path.exists(tuning):
         ctx.load_tuning(tuning)  # the autotuner's split-K table (qlb_autotune on a GB300)
@@ -267,7 +267,9 @@ def _measure_form(args, dev, precision, world, flush):
     nsol = max(1.0, solver["solves"])
     solver_line = {"solves_per_step": solver["solves"] / args.steps, "sweeps_per_solve": solver["sweeps"] / nsol,
                    "mean_n": solver["sum_n"] / nsol, "mean_kept": solver["sum_k"] / nsol,
-                   "at_limit": solver["at_limit"]}
+                   "at_limit": solver["at_limit"],
+                   "zip_range_per_step": solver["zip_range"] / args.steps,
+                   "zip_fallback_per_step": solver["zip_fallback"] / args.steps}
 
     # a later window of the same run: after window2 more steps the bonds have grown
     # to their plateau (the literal dt drives the state into the top Fock levels,
@@ -293,7 +295,8 @@ def _measure_form(args, dev, precision, world, flush):
         n2 = max(1.0, sv2["solves"])
         window2 = {"first_step": args.warmup + args.steps + args.window2, "steps": args.steps,
                    "ms_per_step": sum(ms2) / args.steps, "steps_per_s": args.steps / (sum(ms2) / 1e3),
-                   "bonds": b2, "mean_n": sv2["sum_n"] / n2, "sweeps_per_solve": sv2["sweeps"] / n2}
+                   "bonds": b2, "mean_n": sv2["sum_n"] / n2, "sweeps_per_solve": sv2["sweeps"] / n2,
+                   "zip_fallback_per_step": sv2["zip_fallback"] / args.steps}
 
     # end to end through the public API: host mode vector in (init), K steps each
     # followed by a read-back of the photon number; the system's operators and
@@ -322,7 +325,8 @@ def _measure_form(args, dev, precision, world, flush):
 
 
 FORM_DTYPE = {0: "f64", 1: "f64+df64", 2: "f64+df64+tf32x3"}
-FORM_NAME = {0: "fp64", 1: "mixed (double-float eigen-solves)", 2: "tensor-core (3xTF32 MPO application)"}
+FORM_NAME = {0: "fp64", 1: "mixed (double-float solves and GEMMs, FP64 storage)",
+             2: "tensor-core (3xTF32 MPO application)"}
 
 
 def run_gpu(args):
@@ -359,6 +363,7 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPE[head], "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": 512, "R": 9, "alpha2": 32.0, "eps_z": 0.1, "dt": r["dt"],
                    "chi_max": 64, "chi_mu_max": 16, "tol": 1e-12, "form": FORM_NAME[head],
+                   "mixed_gemm": args.mixed_gemm,
                    "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single", "bonds_before": r["bonds_before"],
                    "bonds_after": r["bonds_after"], "step_status": r["status"]},
@@ -447,6 +452,86 @@ def run_other_workload(args):
     ctx.close()
 
 
+def run_z_gate_sweep(args):
+    """Z gate on a cat qubit with its buffer (Sec. VI numerical experiment): for
+    N_a = 2^R_a memory levels with |alpha|^2 = N_a / 3 (buffer N_b = 16, g2 = 1,
+    kappa_b = 10, eps_Z = 0.04, theta = pi, kappa_a = 0), the even cat is driven for
+    T_Z = theta / (4 alpha eps_Z) with the second-order Kraus scheme at tol 1e-8,
+    chi_mu <= 16.  Reports the phase-flip error p_Z = (1 + <parity>) / 2 (the ideal
+    gate ends in parity -1) beside the paper's p_Z = pi / (40 |alpha|^3), the largest
+    bond seen (the plateau of Fig. Z_gate b) and the time per step."""
+    import torch
+
+    from paper_2605_27515_gb300 import inputs, qlb, systems
+
+    torch.cuda.set_device(0)
+    points = []
+    for Ra in args.z_ra:
+        cfg = inputs.config("z_gate")
+        cfg["R"] = [Ra, 4]
+        cfg["dt"] = args.z_dt
+        ctx = qlb.Ctx(device=0, precision=max(args.precision, 0), tol=cfg["tol"], chi_max=cfg["chi_max"],
+                      chi_mu_max=cfg["chi_mu_max"], stream_ordered=1)
+        b = systems.build(ctx, cfg)
+        b.sys.set_scheme(2)
+        zp = systems.z_gate_params(cfg)
+        st = b.sys.state(b.init)
+        n = zp["steps"]
+        peak_q = peak_mu = 0
+        t0 = time.perf_counter()
+        done = 0
+        while done < n:
+            k = min(100, n - done)
+            st.step(cfg["dt"], k)
+            done += k
+            bd = st.bond_dims()
+            peak_mu, peak_q = max(peak_mu, bd[0]), max(peak_q, max(bd[1:]))
+        ctx.synchronize()
+        wall = time.perf_counter() - t0
+        par = st.expectation(b.observables["parity_a"]).real
+        points.append({"R_a": Ra, "alpha2": zp["alpha2"], "steps": n, "dt": cfg["dt"], "parity_end": par,
+                       "p_Z": (1.0 + par) / 2.0, "p_Z_paper": float(np.pi / (40.0 * zp["alpha"] ** 3)),
+                       "max_chi": peak_q, "max_chi_mu": peak_mu, "ms_per_step": 1e3 * wall / n})
+        st.close()
+        ctx.close()
+    print(json.dumps({"workload": "z_gate_sweep", "scheme": "second-order Kraus", "tol": 1e-8, "chi_mu_max": 16,
+                      "chi_max": 64, "points": points}), flush=True)
+
+
+def run_solver_sweep(args):
+    """Device time of one truncation solve by each kernel (qlb_eig_check) on seeded
+    Gram matrices of the zip-up's kind: G = M M^dag with M of rank n / 2 and
+    singular values graded over 1e-6 (weights over 1e-12), cutoff 1e-18 (the zip-up's
+    tol x 1e-6), in FP64 and double-float.  The step's dispatch thresholds come from
+    this table."""
+    from paper_2605_27515_gb300 import qlb
+
+    names = {qlb.SOLVER_JACOBI: "jacobi_1cta", qlb.SOLVER_CLUSTER8: "jacobi_cluster8",
+             qlb.SOLVER_CLUSTER16: "jacobi_cluster16", qlb.SOLVER_QL: "householder_ql",
+             qlb.SOLVER_RANGE: "range_basis"}
+    rows = []
+    for prec in (qlb.PREC_F64, qlb.PREC_MIXED):
+        for n in args.solver_n:
+            rng = np.random.default_rng(1000 + n)
+            r = max(1, n // 2)
+            M = (rng.normal(size=(n, r)) + 1j * rng.normal(size=(n, r))) * np.logspace(0, -6, r)[None, :]
+            G = M @ M.conj().T
+            G = 0.5 * (G + G.conj().T)
+            row = {"precision": "fp64" if prec == qlb.PREC_F64 else "df64", "n": n}
+            for sv, name in names.items():
+                if (sv == qlb.SOLVER_CLUSTER8 and n > 128) or (sv == qlb.SOLVER_CLUSTER16 and n > 256) or \
+                        (sv == qlb.SOLVER_QL and (prec != qlb.PREC_F64 or n > 64)):
+                    continue
+                best = None
+                for _ in range(3):
+                    _, _, k, ms = qlb.qlb_eig_check(0, prec, sv, G, tol=1e-18, cap=n)
+                    best = ms if best is None else min(best, ms)
+                row[name] = {"ms": best, "k": k}
+            rows.append(row)
+    print(json.dumps({"workload": "solvers", "matrix": "G = M M^dag, rank n/2, weights graded over 1e-12",
+                      "tol": 1e-18, "timing": "best of 3 single launches (CUDA events)", "rows": rows}), flush=True)
+
+
 def serving_summary(dev, n_requests, step_scale, precision, budget_gb=4.0):
     """The serving workload (Poisson arrivals at 200/s of single-cat requests,
     seed 20260527) through the library's continuous-batching server (qlb_server_*):
@@ -481,12 +566,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--window2", type=int, default=200)
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "transmon", "cat_pair"])
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "transmon", "cat_pair", "z_gate_sweep", "solvers"])
+    ap.add_argument("--solver-n", type=int, nargs="+", default=[8, 16, 24, 32, 48, 64, 96, 128, 192, 256])
+    ap.add_argument("--z-ra", type=int, nargs="+", default=[4, 5, 6])
+    ap.add_argument("--z-dt", type=float, default=4e-3)
     ap.add_argument("--serving-step-scale", type=float, default=0.005)
+    ap.add_argument("--mixed-gemm", type=int, default=1, choices=[0, 1, 2],
+                    help="GEMMs of the mixed forms in double-float: 0 none, 1 all but the Grams, 2 all")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "z_gate_sweep":
+        run_z_gate_sweep(args)
+    elif args.workload == "solvers":
+        run_solver_sweep(args)
     elif args.workload != WORKLOAD:
         run_other_workload(args)
     else:

@@ -63,9 +63,10 @@ typedef struct qlb_state qlb_state;
 
 /* Arithmetic of the step. */
 #define QLB_PREC_F64 0   /* every operation in FP64 (the parity form) */
-#define QLB_PREC_MIXED 1 /* the Jacobi truncation solves in double-float (pairs of FP32,
-                            ~48-bit significands) on the FP32 pipes; contractions, Gram
-                            matrices, truncation decisions and renormalisation in FP64 */
+#define QLB_PREC_MIXED 1 /* the truncation solves and the GEMMs chosen by mixed_gemm in
+                            double-float (pairs of FP32, ~48-bit significands) on the FP32
+                            pipes, with FP64 operands and results; truncation decisions,
+                            weights and renormalisation in FP64 */
 #define QLB_PREC_TC 2    /* QLB_PREC_MIXED with the MPO application (the two zip-up
                             contractions of every site) on the tensor cores in 3xTF32
                             (operands split into two TF32 parts, FP32 accumulation);
@@ -89,6 +90,22 @@ typedef struct {
                             it also caps the QL iterations per eigenvalue */
   size_t hbm_budget;     /* bytes of device memory the context may hold; 0 = no limit */
   int stream_ordered;    /* 1: qlb_step only enqueues; 0 (default): it synchronises */
+  int zip_solver;        /* how a zip-up bond finds the range of M: 1 (default) column-
+                            pivoted Gram-Schmidt on G = M M^dag with one
+                            re-orthogonalisation, stopping at the weight cutoff or at the
+                            working precision's rounding level, and the Jacobi eigen-solve
+                            only when the cap is reached first; 0 the Jacobi eigen-solve
+                            on every zip-up bond */
+  int zip_chi_max;       /* cap on the zip-up bonds, in [chi_max, 256]; 0 (default) = chi_max.
+                            The zip-up truncates in a frame that is not orthonormal, so a
+                            cap that binds there costs accuracy that the final sweep cannot
+                            recover */
+  int mixed_gemm;        /* GEMMs of the mixed forms (QLB_PREC_MIXED, QLB_PREC_TC) that multiply
+                            and sum in double-float (~48-bit significands, FP32 pipes) with FP64
+                            operands and results: 0 none (all FP64), 1 (default) the MPO
+                            application and the products of the truncation sweep, 2 also the
+                            Gram matrices the truncations are decided on.  Ignored in QLB_PREC_F64;
+                            in QLB_PREC_TC the MPO application stays on the tensor cores */
 } qlb_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -328,12 +345,15 @@ qlb_status qlb_profile_read(qlb_ctx* ctx, int kclass, double* ms, int64_t* launc
 qlb_status qlb_profile_reset(qlb_ctx* ctx);
 /* Eigen-solver counters of the context since the last qlb_profile_reset, kept
  * whether or not profiling is on (also inside captured step graphs); the first
- * min(n_out, 7) of: out[0] solves, out[1] Jacobi sweeps plus QL passes, out[2] sum
+ * min(n_out, 9) of: out[0] solves, out[1] Jacobi sweeps plus QL passes, out[2] sum
  * of the runtime matrix sizes n, out[3] sum of the kept counts k, out[4] solves
  * that reached the sweep (or QL iteration) limit, out[5] solves whose matrices did
  * not fit in one CTA's shared memory (spread over a thread-block cluster, or in a
- * global-memory workspace), out[6] the largest runtime size n.  Synchronises the
- * device. */
+ * global-memory workspace), out[6] the largest runtime size n, out[7] zip-up range
+ * bases built by pivoted Gram-Schmidt (zip_solver = 1), out[8] of those, the ones
+ * that reached the zip-up cap and left the bond to the Jacobi solve.  A bond the
+ * range basis served counts in out[0], out[2] and out[3] like a solve.
+ * Synchronises the device. */
 qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out, int n_out);
 
 /* Autotuner of the step's launch shapes: times the zip-up Gram GEMM at split-K
@@ -357,6 +377,37 @@ qlb_status qlb_measure_peak(int device, int kind, double* tflops);
  * against an FP64 product.  Copies the operands to device `device`, allocating for the
  * duration of the call.  QLB_ETIMEOUT if a bounded wait of the kernel gave up. */
 qlb_status qlb_tc_zgemm(int device, int m, int n, int k, const double* A, const double* B, double* C);
+
+/* C = A B as above through one of the step's GEMM engines: engine 0 the FP64
+ * work-distributed GEMM, 1 the same GEMM multiplying and summing in double-float
+ * (the mixed forms), 2 the tensor-core 3xTF32 GEMM (as qlb_tc_zgemm).  ms: device
+ * time of one launch (CUDA events, after one untimed launch).  Allocates device
+ * memory for the duration of the call. */
+qlb_status qlb_zgemm_check(int device, int engine, int m, int n, int k, const double* A, const double* B,
+                           double* C, double* ms);
+
+/* One truncation solve of the step, by a named kernel, on a host Hermitian matrix:
+ * exposed so that each solver's numerics and device time can be checked on its
+ * own (Sec. V.A truncated factorisation of a bond through its Gram matrix G).
+ *   precision  QLB_PREC_F64 (FP64 arithmetic) or QLB_PREC_MIXED (double-float)
+ *   solver     0 the kernel the step takes for a planned size n, 1 one-CTA Jacobi,
+ *              2 Jacobi over a cluster of 8 CTAs (n <= 128), 3 over 16 CTAs
+ *              (n <= 256), 4 Householder + implicit QL (FP64 only, n <= 64),
+ *              5 the zip-up range basis (pivoted Gram-Schmidt)
+ *   G          n x n row-major complex128 (2 n^2 doubles), Hermitian, 1 <= n <= 512
+ *   tol, cap   the truncation: relative discarded weight and the cap on k
+ *   lam        n doubles: the eigenvalues, descending, clamped at 0 (solvers 0-4;
+ *              zeros for 5)
+ *   V          n x k kept vectors as columns, row-major complex128 (2 n k doubles
+ *              written, room for 2 n n)
+ *   k_out      the kept count; -1 when solver 5 reached the cap first (the step
+ *              then runs the Jacobi solve)
+ *   ms         device time of one launch (CUDA events, after one untimed launch)
+ * QLB_EINVAL for a solver that does not take this size or precision, QLB_ENOTCONV
+ * at the sweep limit, QLB_ENONFINITE for non-finite input.  Allocates device memory
+ * for the duration of the call. */
+qlb_status qlb_eig_check(int device, int precision, int solver, int n, const double* G, double tol, int cap,
+                         double* lam, double* V, int* k_out, double* ms);
 
 #ifdef __cplusplus
 }

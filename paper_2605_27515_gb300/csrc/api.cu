@@ -130,6 +130,7 @@ qlb_state::~qlb_state() {
   for (auto p : site) dev_free(nullptr, p);
   for (auto p : {X, Mb, G, Cin, Cout, T1, T2, T3, eigw, oE0, oE1, oY, oZ, Wsk}) dev_free(nullptr, p);
   dev_free(nullptr, d_lam);
+  dev_free(nullptr, d_gate);
   dev_free(nullptr, d_stats);
   dev_free(nullptr, d_err);
   dev_free(nullptr, d_step);
@@ -160,6 +161,9 @@ QLB_API void qlb_default_options(qlb_options* o) {
   o->max_sweeps = 40;
   o->hbm_budget = 0;
   o->stream_ordered = 0;
+  o->zip_solver = 1;
+  o->zip_chi_max = 0;
+  o->mixed_gemm = 1;
 }
 
 QLB_API const char* qlb_last_error(void) { return get_error(); }
@@ -178,6 +182,10 @@ QLB_API qlb_status qlb_create(const qlb_options* opt, qlb_ctx** out) {
   CHECK_ARG(o.chi_max >= 1 && o.chi_max <= 256, "chi_max must be in [1, 256]");
   CHECK_ARG(o.chi_mu_max >= 1 && o.chi_mu_max <= 128, "chi_mu_max must be in [1, 128]");
   CHECK_ARG(o.max_sweeps >= 1, "max_sweeps must be >= 1");
+  CHECK_ARG(o.zip_solver == 0 || o.zip_solver == 1, "zip_solver must be 0 or 1");
+  CHECK_ARG(o.mixed_gemm >= 0 && o.mixed_gemm <= 2, "mixed_gemm must be 0, 1 or 2");
+  CHECK_ARG(o.zip_chi_max == 0 || (o.zip_chi_max >= o.chi_max && o.zip_chi_max <= 256),
+            "zip_chi_max must be 0 or in [chi_max, 256]");
   if (o.zip_tol_factor <= 0) o.zip_tol_factor = 1e-6;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
@@ -196,10 +204,11 @@ QLB_API qlb_status qlb_create(const qlb_options* opt, qlb_ctx** out) {
     return QLB_EDEVICE;
   }
   init_kernel_attributes();
+  init_qr_attributes();
   init_tc_attributes();
   {
-    qlb_status st = dev_alloc(c, (void**)&c->d_solver, sizeof(double) * 8);
-    if (st == QLB_OK && cudaMemset(c->d_solver, 0, sizeof(double) * 8) != cudaSuccess) st = QLB_EDEVICE;
+    qlb_status st = dev_alloc(c, (void**)&c->d_solver, sizeof(double) * 16);
+    if (st == QLB_OK && cudaMemset(c->d_solver, 0, sizeof(double) * 16) != cudaSuccess) st = QLB_EDEVICE;
     if (st) {
       cudaStreamDestroy(c->stream);
       delete c;
@@ -919,16 +928,16 @@ QLB_API qlb_status qlb_profile_reset(qlb_ctx* ctx) {
   }
   if (ctx->d_prof) QLB_CUDA_TRY(cudaMemset(ctx->d_prof, 0, sizeof(double) * 2 * QLB_K_COUNT));
   QLB_CUDA_TRY(cudaDeviceSynchronize());
-  if (ctx->d_solver) QLB_CUDA_TRY(cudaMemset(ctx->d_solver, 0, sizeof(double) * 8));
+  if (ctx->d_solver) QLB_CUDA_TRY(cudaMemset(ctx->d_solver, 0, sizeof(double) * 16));
   return QLB_OK;
 }
 
 QLB_API qlb_status qlb_profile_solver_stats(qlb_ctx* ctx, double* out, int n_out) {
   CHECK_ARG(ctx && out && n_out >= 0, "null argument");
   QLB_CUDA_TRY(cudaDeviceSynchronize());
-  double h[8] = {0};
+  double h[16] = {0};
   if (ctx->d_solver) QLB_CUDA_TRY(cudaMemcpy(h, ctx->d_solver, sizeof(h), cudaMemcpyDeviceToHost));
-  for (int i = 0; i < n_out && i < 7; i++) out[i] = h[i];
+  for (int i = 0; i < n_out && i < 9; i++) out[i] = h[i];
   return QLB_OK;
 }
 
@@ -993,6 +1002,202 @@ QLB_API qlb_status qlb_tc_zgemm(int device, int m, int n, int k, const double* A
   }
   if (herr) {
     set_error("qlb_tc_zgemm: a bounded wait for the tensor-core pipeline gave up");
+    return QLB_ETIMEOUT;
+  }
+  return QLB_OK;
+}
+
+// ------------------------------------------------------------------ truncation-solver check
+
+QLB_API qlb_status qlb_eig_check(int device, int precision, int solver, int n, const double* G, double tol, int cap,
+                                 double* lam, double* V, int* k_out, double* ms) {
+  CHECK_ARG(G && lam && V && k_out && ms, "null argument");
+  CHECK_ARG(n >= 1 && n <= 512, "n must be in [1, 512]");
+  CHECK_ARG(precision == QLB_PREC_F64 || precision == QLB_PREC_MIXED, "precision must be F64 or MIXED");
+  CHECK_ARG(solver >= 0 && solver <= 5, "unknown solver");
+  CHECK_ARG(tol >= 0 && tol < 1 && cap >= 1, "bad truncation parameters");
+  CHECK_ARG(solver != 2 || n <= 128, "the 8-CTA cluster solve takes n <= 128");
+  CHECK_ARG(solver != 3 || n <= 256, "the 16-CTA cluster solve takes n <= 256");
+  CHECK_ARG(solver != 4 || (precision == QLB_PREC_F64 && n <= 64), "the QL solve is FP64 with n <= 64");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    set_error("qlb_eig_check: no such CUDA device");
+    return QLB_EDEVICE;
+  }
+  QLB_CUDA_TRY(cudaSetDevice(device));
+  init_kernel_attributes();
+  init_qr_attributes();
+  for (long i = 0; i < 2L * n * n; i++)
+    if (!std::isfinite(G[i])) {
+      set_error("qlb_eig_check: non-finite input");
+      return QLB_ENONFINITE;
+    }
+  const size_t nn = (size_t)n * n;
+  size_t ws = std::max(eig_workspace_elems(n), zipqr_workspace_elems(n));
+  ws = std::max(ws, 2 * (size_t)(n + 1) * (n + 1));  // G and V of the padded size in a global workspace
+  zd *dG = nullptr, *dG0 = nullptr, *dOut = nullptr, *dW = nullptr;
+  double* dLam = nullptr;
+  int *dDims = nullptr, *dErr = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dG);
+    cudaFree(dG0);
+    cudaFree(dOut);
+    cudaFree(dW);
+    cudaFree(dLam);
+    cudaFree(dDims);
+    cudaFree(dErr);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&dG, sizeof(zd) * nn) != cudaSuccess || cudaMalloc(&dG0, sizeof(zd) * nn) != cudaSuccess ||
+      cudaMalloc(&dOut, sizeof(zd) * nn) != cudaSuccess || cudaMalloc(&dW, sizeof(zd) * ws) != cudaSuccess ||
+      cudaMalloc(&dLam, sizeof(double) * n) != cudaSuccess || cudaMalloc(&dDims, sizeof(int) * 4) != cudaSuccess ||
+      cudaMalloc(&dErr, sizeof(int)) != cudaSuccess) {
+    cleanup();
+    set_error("qlb_eig_check: device allocation failed");
+    return QLB_ENOMEM;
+  }
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemcpy(dG0, G, sizeof(zd) * nn, cudaMemcpyHostToDevice);
+  cudaMemset(dLam, 0, sizeof(double) * n);
+  // dims[0] = n, dims[1] = kept count, dims[2] = gate
+  EigDesc e{};
+  e.G = dG;
+  e.n = dconst(n);
+  e.n_max = n;
+  e.out = dOut;
+  e.out_mode = 0;
+  e.dim_out = 1;
+  e.tol = tol;
+  e.cap = dconst(cap);
+  e.gap = 1e-10;
+  e.max_sweeps = 40;
+  e.err = dErr;
+  if (solver != 5) e.lam = dLam;
+  const bool mixed = precision == QLB_PREC_MIXED;
+  cudaError_t r = cudaSuccess;
+  float t = 0.f;
+  for (int rep = 0; rep < 2 && r == cudaSuccess; rep++) {
+    cudaMemcpy(dG, dG0, sizeof(zd) * nn, cudaMemcpyDeviceToDevice);
+    cudaMemset(dDims, 0, sizeof(int) * 4);
+    cudaMemset(dErr, 0, sizeof(int));
+    cudaEventRecord(e0, 0);
+    if (solver == 5) e.gate = dDims + 2;
+    r = launch_solver(mixed, solver, e, dDims, 0, dW);
+    cudaEventRecord(e1, 0);
+    if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+    if (r == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+  }
+  int hd[4] = {0, 0, 0, 0}, herr = 0;
+  if (r == cudaSuccess) r = cudaMemcpy(hd, dDims, sizeof(hd), cudaMemcpyDeviceToHost);
+  if (r == cudaSuccess) r = cudaMemcpy(&herr, dErr, sizeof(int), cudaMemcpyDeviceToHost);
+  const bool gated = solver == 5 && hd[2] != 0;
+  const int k = gated ? 0 : std::max(0, std::min(hd[1], n));
+  if (r == cudaSuccess) r = cudaMemcpy(lam, dLam, sizeof(double) * n, cudaMemcpyDeviceToHost);
+  if (r == cudaSuccess && k > 0) r = cudaMemcpy(V, dOut, sizeof(zd) * (size_t)n * k, cudaMemcpyDeviceToHost);
+  cleanup();
+  if (r != cudaSuccess) {
+    set_error(std::string("qlb_eig_check: ") + cudaGetErrorString(r));
+    return QLB_EDEVICE;
+  }
+  *k_out = gated ? -1 : k;
+  *ms = t;
+  if (herr & 2) {
+    set_error("qlb_eig_check: non-finite values in the solve");
+    return QLB_ENONFINITE;
+  }
+  if (herr & 1) {
+    set_error("qlb_eig_check: the Jacobi solve hit its sweep limit");
+    return QLB_ENOTCONV;
+  }
+  return QLB_OK;
+}
+
+// ------------------------------------------------------------------ GEMM engine check
+
+QLB_API qlb_status qlb_zgemm_check(int device, int engine, int m, int n, int k, const double* A, const double* B,
+                                   double* C, double* ms) {
+  CHECK_ARG(A && B && C && ms, "null argument");
+  CHECK_ARG(engine >= 0 && engine <= 2, "unknown engine");
+  CHECK_ARG(m >= 1 && n >= 1 && k >= 0 && (long)m * n <= (1L << 26) && (long)m * k <= (1L << 26) &&
+                (long)k * n <= (1L << 26),
+            "sizes out of range");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    set_error("qlb_zgemm_check: no such CUDA device");
+    return QLB_EDEVICE;
+  }
+  QLB_CUDA_TRY(cudaSetDevice(device));
+  init_tc_attributes();
+  const size_t nws = gemm_workspace_elems(gemm_grid_default());
+  zd *dA = nullptr, *dB = nullptr, *dC = nullptr, *dW = nullptr;
+  int* derr = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dC);
+    cudaFree(dW);
+    cudaFree(derr);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&dA, sizeof(zd) * std::max<long>(1, (long)m * k)) != cudaSuccess ||
+      cudaMalloc(&dB, sizeof(zd) * std::max<long>(1, (long)k * n)) != cudaSuccess ||
+      cudaMalloc(&dC, sizeof(zd) * (long)m * n) != cudaSuccess || cudaMalloc(&dW, sizeof(zd) * nws) != cudaSuccess ||
+      cudaMalloc(&derr, sizeof(int)) != cudaSuccess) {
+    cleanup();
+    set_error("qlb_zgemm_check: device allocation failed");
+    return QLB_ENOMEM;
+  }
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemcpy(dA, A, sizeof(zd) * (long)m * k, cudaMemcpyHostToDevice);
+  cudaMemcpy(dB, B, sizeof(zd) * (long)k * n, cudaMemcpyHostToDevice);
+  cudaMemset(dW, 0, sizeof(zd) * nws);
+  cudaMemset(derr, 0, sizeof(int));
+  GemmDesc g{};
+  g.A = dA;
+  g.B = dB;
+  g.C = dC;
+  g.m = dconst(m);
+  g.n = dconst(n);
+  g.k = dconst(k);
+  g.lda = dconst(k);
+  g.ldb = dconst(n);
+  g.ldc = dconst(n);
+  g.sA1 = g.sB1 = g.sC1 = g.sA2 = g.sB2 = g.sC2 = dconst(0);
+  g.nb1 = g.nb2 = dconst(1);
+  g.alpha_re = 1.0;
+  g.m_max = m;
+  g.n_max = n;
+  g.nb_max = 1;
+  g.ws = dW;
+  g.df64 = engine == 1;
+  cudaError_t e = cudaSuccess;
+  float t = 0.f;
+  for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+    cudaEventRecord(e0, 0);
+    e = engine == 2 ? launch_gemm_tc(g, nullptr, 0, derr, nullptr) : launch_gemm<double>(g, nullptr, 0, nullptr);
+    cudaEventRecord(e1, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+  }
+  int herr = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(C, dC, sizeof(zd) * (long)m * n, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+  cleanup();
+  if (e != cudaSuccess) {
+    set_error(std::string("qlb_zgemm_check: ") + cudaGetErrorString(e));
+    return QLB_EDEVICE;
+  }
+  *ms = t;
+  if (herr) {
+    set_error("qlb_zgemm_check: a bounded wait for the tensor-core pipeline gave up");
     return QLB_ETIMEOUT;
   }
   return QLB_OK;

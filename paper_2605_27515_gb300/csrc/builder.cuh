@@ -15,13 +15,27 @@ std::map<void*, std::pair<size_t, qlb_ctx*>>& g_alloc_sizes();
 
 template <typename R>
 cudaError_t launch_gemm(const GemmDesc& g, const int* d_dims, cudaStream_t s, double* prof);
+// workspace of the work-distributed GEMM for a grid of `grid` CTAs (complex elements;
+// its counters must start at zero), and the default grid (two CTAs per SM)
+size_t gemm_workspace_elems(int grid);
+int gemm_grid_default();
 template <typename R>
 cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof);
+template <typename R>
+cudaError_t launch_eig_kind(int kind, const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof);
 template <typename R>
 size_t eig_smem_bytes(int n_max);
 // device workspace (complex elements) the eigen-solvers need beyond shared memory
 size_t eig_workspace_elems(int n_max);
 void init_kernel_attributes();
+// zip-up range basis by column-pivoted Gram-Schmidt on the Gram matrix (U and the
+// kept count as launch_eig writes them; the gate tells the Jacobi behind it to run)
+template <typename R>
+cudaError_t launch_zipqr(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof);
+size_t zipqr_workspace_elems(int n_max);
+void init_qr_attributes();
+// a named truncation solver in FP64 or double-float (solver numbering of qlb_eig_check)
+cudaError_t launch_solver(bool mixed, int solver, const EigDesc& e, const int* d_dims, cudaStream_t s, void* work);
 // split-K factor of a (m x m, K) Gram GEMM: the tuned table if it has the bucket,
 // else the built-in rule (about 64 CTAs)
 int gram_splitk(const qlb_ctx* ctx, long m, long K);

@@ -60,6 +60,20 @@ __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
   df_quick_two_sum(p, e, r.hi, r.lo);
   return r;
 }
+// c + a * b with one renormalisation (the product's error terms and the sum's
+// rounding error folded into the low word): the multiply-add of the GEMM
+__device__ __forceinline__ df64 df_mac(df64 c, df64 a, df64 b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  float s, e;
+  df_two_sum(c.hi, p, s, e);
+  e = __fadd_rn(e, __fadd_rn(c.lo, pe));
+  df64 r;
+  df_quick_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
 __device__ __forceinline__ df64 operator/(df64 a, df64 b) {
   // long division: q1 = a/b in float, remainder in double-float, one correction
   float q1 = a.hi / b.hi;

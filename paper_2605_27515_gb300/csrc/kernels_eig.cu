@@ -166,6 +166,7 @@ template <typename R, int NT>
 __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R>* work, int dyn_bytes,
                                            double* prof) {
   extern __shared__ unsigned char smem_raw[];
+  if (e.gate && *e.gate == 0) return;  // the zip-up range basis already served this bond
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
   if (n <= 0) {
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
   __shared__ R s_thr;
   __shared__ double s_tr;
   __shared__ double s_off;
+  __shared__ int s_any;
 
   const zd* G = (const zd*)e.G;
   for (long x = tid; x < (long)np * np; x += NT) {
@@ -302,6 +304,20 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
     total_rot += nr;
     __syncthreads();
     if (nr == 0) break;
+    // A sweep that rotates nothing leaves G as it is, so it rotates nothing exactly
+    // when no pair passes the rotation test on the current G: test every pair at
+    // once (the same expressions) instead of spending a sweep of rounds on it.
+    if (tid == 0) s_any = 0;
+    __syncthreads();
+    for (long w = tid; w < (long)n * n; w += NT) {
+      const int p = (int)(w / n), q = (int)(w - (long)p * n);
+      if (q <= p) continue;
+      R a = Gs[(long)p * np + p].re, b = Gs[(long)q * np + q].re;
+      R x = sqrt(cabs2(Gs[(long)p * np + q]));
+      if (x > rel_tol * sqrt(fabs(a * b)) && x > abs_thr && x > zero) s_any = 1;
+    }
+    __syncthreads();
+    if (!s_any) break;
   }
   bool unconverged = false;
   const bool at_limit = sweep >= e.max_sweeps;
@@ -365,6 +381,7 @@ __global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, d
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ unsigned char smem_raw[];
+  if (e.gate && *e.gate == 0) return;  // the zip-up range basis already served this bond
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
   const int rank = (int)cluster.block_rank();
@@ -381,7 +398,7 @@ __global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, d
   cx<R>* Gb1 = Gb0 + (long)rpb * np;
   cx<R>* Vl = Gb1 + (long)rpb * np;
   __shared__ JRot<R> rot[EIG_CL_MAX_NP / 2];
-  __shared__ int cnt[2];
+  __shared__ int cnt[2], chk[2];
   __shared__ double s_part;
   __shared__ double s_lam[EIG_CL_MAX_NP];
   __shared__ int s_perm[EIG_CL_MAX_NP];
@@ -507,6 +524,27 @@ __global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, d
     for (int k = 0; k < C; k++) nr += *cluster.map_shared_rank(&cnt[par], k);
     total_rot += nr;
     if (nr == 0) break;
+    // as in the one-CTA solve: a sweep would rotate nothing exactly when no pair
+    // passes the test on the current G; each CTA tests the pairs of its rows
+    {
+      const cx<R>* Gc = cur ? Gb1 : Gb0;
+      if (tid == 0) chk[par] = 0;
+      __syncthreads();
+      for (long w = tid; w < (long)nloc * np; w += NT) {
+        const int li = (int)(w / np), q = (int)(w - (long)li * np);
+        const int p = r0 + li;
+        if (p >= n || q >= n || q <= p) continue;
+        const int oq = q / rpb;
+        R a = Gc[(long)li * np + p].re;
+        R b = cluster.map_shared_rank(Gc, oq)[(long)(q - oq * rpb) * np + q].re;
+        R x = sqrt(cabs2(Gc[(long)li * np + q]));
+        if (x > rel_tol * sqrt(fabs(a * b)) && x > abs_thr && x > zero) chk[par] = 1;
+      }
+      cluster.sync();
+      int any = 0;
+      for (int k = 0; k < C; k++) any += *cluster.map_shared_rank(&chk[par], k);
+      if (!any) break;
+    }
   }
   cx<R>* Gc = cur ? Gb1 : Gb0;
   bool unconverged = false;
@@ -638,6 +676,7 @@ constexpr int HEEV_MAX_IT = 60;
 template <int NT>
 __global__ void __launch_bounds__(NT) k_heev(EigDesc e, int* __restrict__ d, zd* work, int dyn_bytes, double* prof) {
   extern __shared__ unsigned char smem_raw[];
+  if (e.gate && *e.gate == 0) return;  // the zip-up range basis already served this bond
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -938,21 +977,14 @@ cudaError_t launch_eig_cl(const EigDesc& e, const int* d_dims, cudaStream_t s, d
 
 template <typename R>
 cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof) {
-  if (std::is_same<R, double>::value && e.n_max <= HEEV_N_MAX) {
-    // FP64, planned sizes up to 64: Householder tridiagonalisation + implicit QL in
-    // one CTA.  Larger planned sizes stay on Jacobi even when the runtime size is
-    // small: on the literal cat_r9 step (which amplifies high-Fock components ~65x
-    // per step) the QL vectors' absolute accuracy seeded the blow-up within 30
-    // steps, while Jacobi's relative accuracy on the graded Gram matrices kept the
-    // state on the dense oracle (measured on GB300).
-    size_t want = eig_smem_bytes<double>(e.n_max);
-    int dyn = (int)(want <= HEEV_SMEM_LIMIT ? want : HEEV_SMEM_LIMIT);
-    k_heev<128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
-    return cudaGetLastError();
-  }
-  // planned sizes past one SM's worth of work: Jacobi over a thread-block cluster
-  // (rows of G and V in distributed shared memory)
-  if (e.n_max > (std::is_same<R, double>::value ? HEEV_N_MAX : 24) && e.n_max <= EIG_CL_MAX_NP) {
+  // Jacobi in both precisions.  The Householder + QL solve (k_heev) is not used by
+  // the step: on the literal cat_r9 map its absolute-accuracy vectors seeded a
+  // blow-up that Jacobi's relative accuracy does not, and on the exactly structured
+  // Gram matrices of the transmon eigenbasis (rank-one 4 x 4) it hit its iteration
+  // limit with a non-finite eigenvalue; the solver sweep on GB300 (qlb_eig_check)
+  // has it no faster than Jacobi above n = 8.  Planned sizes above 24: Jacobi over
+  // a thread-block cluster (rows of G and V in distributed shared memory).
+  if (e.n_max > 24 && e.n_max <= EIG_CL_MAX_NP) {
     if (e.n_max <= 128) return launch_eig_cl<R, 8>(e, d_dims, s, prof);
     return launch_eig_cl<R, 16>(e, d_dims, s, prof);
   }
@@ -972,6 +1004,36 @@ cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void
 }
 template cudaError_t launch_eig<double>(const EigDesc&, const int*, cudaStream_t, void*, double*);
 template cudaError_t launch_eig<df64>(const EigDesc&, const int*, cudaStream_t, void*, double*);
+
+// One named solver regardless of the size rule above (the check entry point):
+// 1 one-CTA Jacobi, 2 cluster Jacobi over 8 CTAs (n <= 128), 3 over 16 CTAs
+// (n <= 256), 4 Householder + QL (FP64, n <= 64).
+template <typename R>
+cudaError_t launch_eig_kind(int kind, const EigDesc& e, const int* d_dims, cudaStream_t s, void* work,
+                            double* prof) {
+  if (kind == 2 && e.n_max <= 128) return launch_eig_cl<R, 8>(e, d_dims, s, prof);
+  if (kind == 3 && e.n_max <= EIG_CL_MAX_NP) return launch_eig_cl<R, 16>(e, d_dims, s, prof);
+  if (kind == 4 && std::is_same<R, double>::value && e.n_max <= HEEV_N_MAX) {
+    size_t want = eig_smem_bytes<double>(e.n_max);
+    int dyn = (int)(want <= HEEV_SMEM_LIMIT ? want : HEEV_SMEM_LIMIT);
+    k_heev<128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (zd*)work, dyn, prof);
+    return cudaGetLastError();
+  }
+  if (kind == 1) {
+    size_t want = eig_smem_bytes<R>(e.n_max);
+    int dyn = (int)(want <= EIG_SMEM_LIMIT ? want : EIG_SMEM_LIMIT);
+    if (e.n_max <= 24)
+      k_eig<R, 128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+    else if (std::is_same<R, df64>::value)
+      k_eig<R, 1024><<<1, 1024, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+    else
+      k_eig<R, 512><<<1, 512, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
+}
+template cudaError_t launch_eig_kind<double>(int, const EigDesc&, const int*, cudaStream_t, void*, double*);
+template cudaError_t launch_eig_kind<df64>(int, const EigDesc&, const int*, cudaStream_t, void*, double*);
 
 void init_kernel_attributes() {
   set_attr<double, 128>();

@@ -1,20 +1,32 @@
 // Batched complex GEMM of the step whose shapes are read from device memory,
 // templated on the real type (double for the FP64 form, float for FP32 parts).
+//
+// The step's GEMMs are small and their sizes change every step (bond dimensions
+// live in device memory), while the launch configuration is fixed when the step is
+// captured as a CUDA graph.  On this GPU one SM retires ~2 FP64 FMAs per clock, so
+// a GEMM whose 32 x 32 output tiles cover only a few SMs runs at a few percent of
+// the chip.  The kernel is therefore persistent over a fixed grid (two CTAs per SM
+// when a workspace is given) and decides the decomposition at run time from the
+// actual sizes: with T output tiles and G CTAs it splits the K range into
+// s = min(G / T, ceil(K / 16), cap) parts, so that T * s work items keep the SMs
+// busy.  Each (tile, part) item writes its partial tile to the workspace; the CTA
+// that finishes a tile last (a per-tile counter, no waiting) adds the s partials in
+// part order and applies alpha and beta, so the result does not depend on timing.
 
 #include <algorithm>
 #include <cfloat>
+#include <type_traits>
 
+#include "df64.cuh"
 #include "qlb_internal.cuh"
 
 namespace qlb {
 
-// =====================================================================================
-// batched complex GEMM, shapes from device memory
-// =====================================================================================
-
 namespace {
 
 constexpr int GB_M = 32, GB_N = 32, GB_K = 16, G_THREADS = 256;
+constexpr int GB_TILE = GB_M * GB_N;
+constexpr int GB_SPLIT_CAP = 64;  // default cap on the K split
 
 template <typename R>
 __device__ __forceinline__ cx<R> ldop(const cx<R>* P, int op, long ld, int i, int k) {
@@ -25,168 +37,226 @@ __device__ __forceinline__ cx<R> ldop(const cx<R>* P, int op, long ld, int i, in
   return v;
 }
 
+// storage -> compute type of an operand, compute -> storage type of a result
+template <typename C, typename S>
+__device__ __forceinline__ cx<C> to_c(cx<S> v) {
+  return mk<C>(C(v.re), C(v.im));
+}
+template <typename S, typename C>
+__device__ __forceinline__ cx<S> to_s(cx<C> v) {
+  return mk<S>((S)v.re, (S)v.im);
+}
+// a partial tile entry written by another CTA of this launch (past L1)
+__device__ __forceinline__ cx<double> ldcg_cx(const cx<double>* p) { return mk<double>(__ldcg(&p->re), __ldcg(&p->im)); }
+__device__ __forceinline__ cx<float> ldcg_cx(const cx<float>* p) { return mk<float>(__ldcg(&p->re), __ldcg(&p->im)); }
+__device__ __forceinline__ cx<df64> ldcg_cx(const cx<df64>* p) {
+  const float4 v = __ldcg((const float4*)p);
+  return mk<df64>(df64(v.x, v.y), df64(v.z, v.w));
+}
+// acc += a * b
+template <typename C>
+__device__ __forceinline__ void cmac(cx<C>& acc, cx<C> a, cx<C> b) {
+  cfma(acc, a, b);
+}
+template <>
+__device__ __forceinline__ void cmac<df64>(cx<df64>& acc, cx<df64> a, cx<df64> b) {
+  acc.re = df_mac(acc.re, a.re, b.re);
+  acc.re = df_mac(acc.re, -a.im, b.im);
+  acc.im = df_mac(acc.im, a.re, b.im);
+  acc.im = df_mac(acc.im, a.im, b.re);
+}
+
 template <typename R>
+__device__ __forceinline__ cx<R> gemm_alpha(const GemmDesc& g) {
+  cx<R> alpha = mk<R>((R)g.alpha_re, (R)g.alpha_im);
+  if (g.alpha_scale) {
+    double s = *g.alpha_scale;
+    if (g.alpha_scale_rsqrt) s = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
+    alpha = cscale(alpha, (R)s);
+  }
+  return alpha;
+}
+
+// R: the storage type of A, B, C; Cm: the type the products are formed and summed in
+// (R itself, or double-float for FP64 storage in the mixed forms)
+template <typename R, typename Cm>
 __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc g, const int* __restrict__ d, double* prof) {
   const int m = dev_eval(g.m, d), n = dev_eval(g.n, d), K = dev_eval(g.k, d);
   const int nb1 = dev_eval(g.nb1, d), nb2 = dev_eval(g.nb2, d);
-  const int nsplit = g.ksplit > 1 ? g.ksplit : 1;
-  const int bz = blockIdx.z / nsplit, ks = blockIdx.z - (blockIdx.z / nsplit) * nsplit;
-  if (bz >= nb1 * nb2 || m <= 0 || n <= 0) return;
-  const int row0 = blockIdx.y * GB_M, col0 = blockIdx.x * GB_N;
-  if (row0 >= m || col0 >= n) return;
-  const int b1 = bz / nb2, b2 = bz - b1 * nb2;
-  const long lda = dev_eval(g.lda, d), ldb = dev_eval(g.ldb, d), ldc = dev_eval(g.ldc, d);
-  const cx<R>* A = (const cx<R>*)g.A + (long)b1 * dev_eval(g.sA1, d) + (long)b2 * dev_eval(g.sA2, d);
-  const cx<R>* B = (const cx<R>*)g.B + (long)b1 * dev_eval(g.sB1, d) + (long)b2 * dev_eval(g.sB2, d);
-  cx<R>* C = (cx<R>*)g.C + (long)b1 * dev_eval(g.sC1, d) + (long)b2 * dev_eval(g.sC2, d);
-
-  // K range of this CTA (the whole range without split-K)
-  int kbeg = 0, kend = K;
-  if (nsplit > 1) {
-    const int chunk = (((K + nsplit - 1) / nsplit) + GB_K - 1) / GB_K * GB_K;
-    kbeg = min(K, ks * chunk);
-    kend = min(K, kbeg + chunk);
+  const int nb = nb1 * nb2;
+  if (m <= 0 || n <= 0 || nb <= 0) return;
+  const int tm = (m + GB_M - 1) / GB_M, tn = (n + GB_N - 1) / GB_N;
+  const long ntiles = (long)tm * tn * nb;
+  // the K split of this launch, from the run-time sizes (the same in every CTA)
+  int ks = 1;
+  if (g.ws && K > GB_K && ntiles < (long)gridDim.x) {
+    const int cap = g.ksplit >= 1 ? g.ksplit : GB_SPLIT_CAP;
+    ks = (int)min((long)cap, (long)gridDim.x / ntiles);
+    ks = min(ks, (K + GB_K - 1) / GB_K);
+    if (ks < 1) ks = 1;
   }
-  if (prof && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
-    double nb = (double)(nb1 * nb2);
+  const int chunk = ks > 1 ? (((K + ks - 1) / ks + GB_K - 1) / GB_K) * GB_K : K;
+  if (ks > 1) ks = (K + chunk - 1) / chunk;
+  if (prof && blockIdx.x == 0 && threadIdx.x == 0) {
     atomicAdd(prof, 8.0 * (double)m * (double)n * (double)K * nb);
     atomicAdd(prof + QLB_K_COUNT, (double)sizeof(cx<R>) * ((double)m * K + (double)K * n + (double)m * n) * nb);
   }
+  const long lda = dev_eval(g.lda, d), ldb = dev_eval(g.ldb, d), ldc = dev_eval(g.ldc, d);
+  cx<Cm>* part_ws = (cx<Cm>*)g.ws;
+  int* counters = g.ws ? (int*)(part_ws + (long)gridDim.x * GB_TILE) : nullptr;
 
-  __shared__ cx<R> As[GB_K][GB_M + 1];
-  __shared__ cx<R> Bs[GB_K][GB_N + 1];
+  __shared__ cx<Cm> As[GB_K][GB_M + 1];
+  __shared__ cx<Cm> Bs[GB_K][GB_N + 1];
+  __shared__ int s_last;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  cx<R> acc[2][2];
-#pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int j = 0; j < 2; j++) acc[i][j] = mk<R>(0, 0);
+  const long items = ntiles * ks;
+  for (long it = blockIdx.x; it < items; it += gridDim.x) {
+    const long tile = it / ks;
+    const int kp = (int)(it - tile * ks);
+    const int bz = (int)(tile / ((long)tm * tn));
+    const int t2 = (int)(tile - (long)bz * tm * tn);
+    const int row0 = (t2 / tn) * GB_M, col0 = (t2 % tn) * GB_N;
+    const int b1 = bz / nb2, b2 = bz - b1 * nb2;
+    const cx<R>* A = (const cx<R>*)g.A + (long)b1 * dev_eval(g.sA1, d) + (long)b2 * dev_eval(g.sA2, d);
+    const cx<R>* B = (const cx<R>*)g.B + (long)b1 * dev_eval(g.sB1, d) + (long)b2 * dev_eval(g.sB2, d);
+    cx<R>* C = (cx<R>*)g.C + (long)b1 * dev_eval(g.sC1, d) + (long)b2 * dev_eval(g.sC2, d);
+    const int kbeg = kp * chunk, kend = min(K, kbeg + chunk);
 
-  for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
-    // A tile: rows row0.., cols k0..
-    for (int e = tid; e < GB_M * GB_K; e += G_THREADS) {
-      int i, kk;
-      if (g.opA == OP_N) {
-        kk = e % GB_K;
-        i = e / GB_K;
-      } else {
-        i = e % GB_M;
-        kk = e / GB_M;
-      }
-      int gi = row0 + i, gk = k0 + kk;
-      As[kk][i] = (gi < m && gk < kend) ? ldop(A, g.opA, lda, gi, gk) : mk<R>(0, 0);
-    }
-    for (int e = tid; e < GB_N * GB_K; e += G_THREADS) {
-      int j, kk;
-      if (g.opB == OP_N) {
-        j = e % GB_N;
-        kk = e / GB_N;
-      } else {
-        kk = e % GB_K;
-        j = e / GB_K;
-      }
-      int gj = col0 + j, gk = k0 + kk;
-      // op(B)(k, j): OP_N B[k*ldb + j]; OP_T B[j*ldb + k]
-      cx<R> v = mk<R>(0, 0);
-      if (gj < n && gk < kend) {
-        if (g.opB == OP_N)
-          v = B[(long)gk * ldb + gj];
-        else {
-          v = B[(long)gj * ldb + gk];
-          if (g.opB == OP_C) v.im = -v.im;
-        }
-      }
-      Bs[kk][j] = v;
-    }
-    __syncthreads();
+    cx<Cm> acc[2][2];
 #pragma unroll
-    for (int kk = 0; kk < GB_K; kk++) {
-      cx<R> a0 = As[kk][ty], a1 = As[kk][ty + 16];
-      cx<R> b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
-      cfma(acc[0][0], a0, b0);
-      cfma(acc[0][1], a0, b1);
-      cfma(acc[1][0], a1, b0);
-      cfma(acc[1][1], a1, b1);
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+      for (int j = 0; j < 2; j++) acc[i][j] = to_c<Cm>(mk<R>(0, 0));
+    for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
+      // A tile: rows row0.., cols k0..
+      for (int e = tid; e < GB_M * GB_K; e += G_THREADS) {
+        int i, kk;
+        if (g.opA == OP_N) {
+          kk = e % GB_K;
+          i = e / GB_K;
+        } else {
+          i = e % GB_M;
+          kk = e / GB_M;
+        }
+        int gi = row0 + i, gk = k0 + kk;
+        As[kk][i] = to_c<Cm>((gi < m && gk < kend) ? ldop(A, g.opA, lda, gi, gk) : mk<R>(0, 0));
+      }
+      for (int e = tid; e < GB_N * GB_K; e += G_THREADS) {
+        int j, kk;
+        if (g.opB == OP_N) {
+          j = e % GB_N;
+          kk = e / GB_N;
+        } else {
+          kk = e % GB_K;
+          j = e / GB_K;
+        }
+        int gj = col0 + j, gk = k0 + kk;
+        // op(B)(k, j): OP_N B[k*ldb + j]; OP_T B[j*ldb + k]
+        cx<R> v = mk<R>(0, 0);
+        if (gj < n && gk < kend) {
+          if (g.opB == OP_N)
+            v = B[(long)gk * ldb + gj];
+          else {
+            v = B[(long)gj * ldb + gk];
+            if (g.opB == OP_C) v.im = -v.im;
+          }
+        }
+        Bs[kk][j] = to_c<Cm>(v);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < GB_K; kk++) {
+        cx<Cm> a0 = As[kk][ty], a1 = As[kk][ty + 16];
+        cx<Cm> b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+        cmac(acc[0][0], a0, b0);
+        cmac(acc[0][1], a0, b1);
+        cmac(acc[1][0], a1, b0);
+        cmac(acc[1][1], a1, b1);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-  }
-  if (nsplit > 1) {
-    // partial sums of this K range; the reduction applies alpha and beta
-    cx<R>* W = (cx<R>*)g.ws + ((long)ks * g.nb_max + bz) * (long)g.m_max * g.n_max;
+    if (ks > 1) {
+      // partial tile of this K part; the last CTA of the tile adds them in order
+      cx<Cm>* P = part_ws + ((long)kp * ntiles + tile) * GB_TILE;
+#pragma unroll
+      for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) P[(ty + 16 * i) * GB_N + tx + 16 * j] = acc[i][j];
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) s_last = atomicAdd(counters + tile, 1) == ks - 1;
+      __syncthreads();
+      if (!s_last) continue;
+      __threadfence();
+#pragma unroll
+      for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+          cx<Cm> sum = to_c<Cm>(mk<R>(0, 0));
+          const long off = (long)(ty + 16 * i) * GB_N + tx + 16 * j;
+          for (int s = 0; s < ks; s++) {
+            const cx<Cm>* Ps = part_ws + ((long)s * ntiles + tile) * GB_TILE + off;
+            sum = cadd(sum, ldcg_cx(Ps));
+          }
+          acc[i][j] = sum;
+        }
+      if (tid == 0) counters[tile] = 0;  // ready for the next launch on this workspace
+    }
+    const cx<R> alpha = gemm_alpha<R>(g);
 #pragma unroll
     for (int i = 0; i < 2; i++)
 #pragma unroll
       for (int j = 0; j < 2; j++) {
         int gi = row0 + ty + 16 * i, gj = col0 + tx + 16 * j;
-        if (gi < m && gj < n) W[(long)gi * g.n_max + gj] = acc[i][j];
+        if (gi < m && gj < n) {
+          cx<R> v = cmul(alpha, to_s<R>(acc[i][j]));
+          cx<R>* dst = C + (long)gi * ldc + gj;
+          if (g.beta) v = cadd(v, *dst);
+          *dst = v;
+        }
       }
-    return;
-  }
-  cx<R> alpha = mk<R>((R)g.alpha_re, (R)g.alpha_im);
-  if (g.alpha_scale) {
-    double s = *g.alpha_scale;
-    if (g.alpha_scale_rsqrt) s = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
-    alpha = cscale(alpha, (R)s);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int j = 0; j < 2; j++) {
-      int gi = row0 + ty + 16 * i, gj = col0 + tx + 16 * j;
-      if (gi < m && gj < n) {
-        cx<R> v = cmul(alpha, acc[i][j]);
-        cx<R>* dst = C + (long)gi * ldc + gj;
-        if (g.beta) v = cadd(v, *dst);
-        *dst = v;
-      }
-    }
-}
-
-// C = alpha * sum_s W[s] (+ C): the split-K partial sums added in split order.
-template <typename R>
-__global__ void k_gemm_splitk_sum(GemmDesc g, const int* __restrict__ d) {
-  const int m = dev_eval(g.m, d), n = dev_eval(g.n, d);
-  const int nb1 = dev_eval(g.nb1, d), nb2 = dev_eval(g.nb2, d);
-  const long ldc = dev_eval(g.ldc, d);
-  cx<R> alpha = mk<R>((R)g.alpha_re, (R)g.alpha_im);
-  if (g.alpha_scale) {
-    double s = *g.alpha_scale;
-    if (g.alpha_scale_rsqrt) s = (s > 0.0) ? 1.0 / sqrt(s) : 0.0;
-    alpha = cscale(alpha, (R)s);
-  }
-  const long per = (long)m * n, total = per * nb1 * nb2;
-  const long slab = (long)g.m_max * g.n_max;
-  for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
-    const int bz = (int)(x / per);
-    const long r = x - (long)bz * per;
-    const int i = (int)(r / n), j = (int)(r - (long)i * n);
-    const int b1 = bz / nb2, b2 = bz - b1 * nb2;
-    cx<R> acc = mk<R>(0, 0);
-    for (int s = 0; s < g.ksplit; s++) acc = cadd(acc, ((const cx<R>*)g.ws)[((long)s * g.nb_max + bz) * slab + (long)i * g.n_max + j]);
-    cx<R>* C = (cx<R>*)g.C + (long)b1 * dev_eval(g.sC1, d) + (long)b2 * dev_eval(g.sC2, d);
-    cx<R> v = cmul(alpha, acc);
-    if (g.beta) v = cadd(v, C[(long)i * ldc + j]);
-    C[(long)i * ldc + j] = v;
   }
 }
 
 }  // namespace
 
+size_t gemm_workspace_elems(int grid) {
+  // grid partial tiles, then one counter (int) per tile, rounded up to whole elements
+  return (size_t)grid * GB_TILE + ((size_t)grid * sizeof(int) + sizeof(zd) - 1) / sizeof(zd);
+}
+
+int gemm_grid_default() {
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) {
+      cudaGetLastError();
+      sms = 148;
+    }
+    grid = 2 * sms;
+  }
+  return grid;
+}
+
 template <typename R>
 cudaError_t launch_gemm(const GemmDesc& g, const int* d_dims, cudaStream_t s, double* prof) {
-  const int nsplit = g.ksplit > 1 && g.ws ? g.ksplit : 1;
+  const long planned = (long)((g.m_max + GB_M - 1) / GB_M) * ((g.n_max + GB_N - 1) / GB_N) *
+                       (g.nb_max > 0 ? g.nb_max : 1);
+  if (planned <= 0) return cudaSuccess;
+  // with a workspace: a fixed grid that the run-time split fills; without: one CTA
+  // per planned tile (persistent above 4096)
+  const int grid = g.ws ? (g.grid > 0 ? g.grid : gemm_grid_default()) : (int)std::min<long>(planned, 4096);
   GemmDesc gg = g;
-  gg.ksplit = nsplit;
-  const int nb = g.nb_max > 0 ? g.nb_max : 1;
-  dim3 grid((g.n_max + GB_N - 1) / GB_N, (g.m_max + GB_M - 1) / GB_M, nb * nsplit);
-  if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-  k_gemm<R><<<grid, G_THREADS, 0, s>>>(gg, d_dims, prof);
-  if (nsplit > 1) {
-    long total = (long)g.m_max * g.n_max * nb;
-    unsigned blocks = (unsigned)std::min<long>(4 * 152, (total + 255) / 256);
-    k_gemm_splitk_sum<R><<<blocks, 256, 0, s>>>(gg, d_dims);
+  if (!g.ws) gg.ksplit = 1;
+  if constexpr (std::is_same<R, double>::value) {
+    if (g.df64) {
+      k_gemm<R, df64><<<grid, G_THREADS, 0, s>>>(gg, d_dims, prof);
+      return cudaGetLastError();
+    }
   }
+  k_gemm<R, R><<<grid, G_THREADS, 0, s>>>(gg, d_dims, prof);
   return cudaGetLastError();
 }
 

@@ -112,11 +112,17 @@ struct GemmDesc {
   // caps on the grid (host-known maxima)
   int m_max, n_max, nb_max;
   int kclass;  // profiling class
-  // split-K: ksplit > 1 spreads the K range over ksplit CTAs per output tile; the
-  // partial sums go to ws ([ksplit][nb_max][m_max][n_max] complex) and a second
-  // kernel adds them in a fixed order and applies alpha and beta (deterministic)
+  // Work distribution.  Without ws: one CTA per planned output tile.  With ws (at
+  // least gemm_workspace_elems(grid) complex elements, zeroed once): a fixed grid of
+  // `grid` CTAs (0 = two per SM) that splits the K range at run time so that tiles x
+  // parts fill it; ksplit >= 1 caps that split (0: the default cap).  The last CTA of a tile adds the
+  // partials in part order (deterministic).
   int ksplit;
   void* ws;
+  int grid;
+  // 1: FP64 operands multiplied and summed in double-float (~48-bit significands) on
+  // the FP32 pipes; the result is stored in FP64
+  int df64;
 };
 
 // Hermitian eigen solve + truncation select (one CTA per problem).
@@ -141,6 +147,8 @@ struct EigDesc {
   double* disc_stat;    // optional: running max of discarded relative weight
   int* err;             // error flags (bit 0: no convergence, bit 1: non-finite)
   double* solver_stats; // optional counters (see qlb_ctx::d_solver)
+  int* gate;            // optional: when set, the eigen-solve runs only if *gate != 0
+                        // (the zip-up range basis sets it when its cap was reached)
 };
 
 // ------------------------------------------------------------------ error plumbing

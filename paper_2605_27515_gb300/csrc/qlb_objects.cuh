@@ -153,6 +153,7 @@ struct qlb_state {
   qlb::zd* Wsk = nullptr;
   size_t nWsk = 0;
   double* d_lam = nullptr;
+  int* d_gate = nullptr;  // zip-up range basis -> Jacobi solve behind it (1: run)
   double* d_stats = nullptr;  // [0] kept weight (mu), [1] total weight (mu), [2] max disc, [3] scratch
   int* d_err = nullptr;
   long long* d_step = nullptr;  // steps taken (drive table index)

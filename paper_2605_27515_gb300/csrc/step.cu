@@ -169,8 +169,8 @@ static void prof_after(qlb_ctx* ctx, cudaStream_t sm, int kclass, cudaEvent_t a)
 
 #ifdef QLB_DEBUG_DUMP
 // Debug builds only (compiled with -DQLB_DEBUG_DUMP): with QLB_DEBUG_DUMP=<file> in
-// the environment, append the dims array and the first entries of the output after
-// every launch of an uncaptured step.
+// the environment, append the dims array, the error flags and the first entries of
+// the output after every launch of an uncaptured step.
 static FILE* debug_file() {
   static FILE* f = nullptr;
   static bool init = false;
@@ -191,6 +191,8 @@ static void debug_dump(qlb_state* st, int tag, const void* out) {
   int n = 2 * st->L + 2;
   std::vector<int> d(n);
   cudaMemcpy(d.data(), st->d_dims, sizeof(int) * n, cudaMemcpyDeviceToHost);
+  int err = 0;
+  cudaMemcpy(&err, st->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   std::vector<zd> buf(64, mk<double>(0, 0));
   auto it = g_alloc_sizes().find(const_cast<void*>(out));
   size_t avail = it == g_alloc_sizes().end() ? 0 : it->second.first / sizeof(zd);
@@ -198,6 +200,7 @@ static void debug_dump(qlb_state* st, int tag, const void* out) {
   fwrite(&tag, sizeof(int), 1, f);
   fwrite(&n, sizeof(int), 1, f);
   fwrite(d.data(), sizeof(int), n, f);
+  fwrite(&err, sizeof(int), 1, f);
   fwrite(buf.data(), sizeof(zd), 64, f);
   fflush(f);
 }
@@ -211,6 +214,10 @@ static qlb_status gemm(qlb_state* st, GemmDesc& g) {
   cudaEvent_t a;
   prof_before(ctx, st->stream, g.kclass, &a);
   double* pf = ctx->prof_on ? ctx->d_prof + g.kclass : nullptr;
+  if (!g.ws && st->Wsk && st->nWsk >= gemm_workspace_elems(gemm_grid_default())) g.ws = st->Wsk;
+  // the mixed forms multiply in double-float (FP64 operands and results)
+  if (st->prec != QLB_PREC_F64)
+    g.df64 = ctx->opt.mixed_gemm >= 2 || (ctx->opt.mixed_gemm == 1 && g.kclass != QLB_K_GRAM);
   // the tensor-core form runs the MPO application (the zip-up contractions) in
   // 3xTF32 on tcgen05; everything feeding a truncation decision stays FP64
   cudaError_t e = (st->prec == QLB_PREC_TC && g.kclass == QLB_K_CONTRACT)
@@ -241,6 +248,28 @@ static qlb_status eig(qlb_state* st, EigDesc& e) {
   }
   debug_dump(st, 2, e.out);
   return QLB_OK;
+}
+
+// A zip-up bond needs only an orthonormal basis of the range of M at the zip-up
+// cutoff: the pivoted Gram-Schmidt basis first; the Jacobi solve behind it runs
+// (through the gate) only when the basis reached the cap before the cutoff.
+static qlb_status zip_range(qlb_state* st, EigDesc& e) {
+  qlb_ctx* ctx = st->sys->ctx;
+  if (!ctx->opt.zip_solver) return eig(st, e);
+  cudaEvent_t a;
+  prof_before(ctx, st->stream, QLB_K_EIG, &a);
+  double* pf = ctx->prof_on ? ctx->d_prof + QLB_K_EIG : nullptr;
+  e.solver_stats = ctx->d_solver;
+  e.gate = st->d_gate;
+  cudaError_t r = st->prec != QLB_PREC_F64 ? launch_zipqr<df64>(e, st->d_dims, st->stream, st->eigw, pf)
+                                           : launch_zipqr<double>(e, st->d_dims, st->stream, st->eigw, pf);
+  prof_after(ctx, st->stream, QLB_K_EIG, a);
+  if (r != cudaSuccess) {
+    set_error(std::string("zip-up range basis launch: ") + cudaGetErrorString(r));
+    return QLB_EDEVICE;
+  }
+  debug_dump(st, 3, e.out);
+  return eig(st, e);
 }
 
 static qlb_status copy(qlb_state* st, zd* dst, const zd* src, DimExpr cnt, long max_n) {
@@ -592,8 +621,10 @@ static Caps compute_caps(const qlb_state* st, const std::vector<int>& cur, const
   // zip-up bond i: rank(M) <= min(2 z_{i-1}, d_i D_i).  It is not bounded by the
   // right Hilbert dimension 2^(L-i): the right environment of the zip-up holds
   // the MPO and is no isometry, so M can need more columns than the final Schmidt rank.
+  const qlb_options& o = st->sys->ctx->opt;
+  const long zip_cap = o.zip_chi_max > 0 ? std::max(o.zip_chi_max, st->cap_chi) : st->cap_chi;
   for (int i = 1; i < L; i++) {
-    long v = std::min<long>({(long)st->cap_chi, 2L * c.zcap[i - 1], (long)c.dcap[i] * K.D[i]});
+    long v = std::min<long>({zip_cap, 2L * c.zcap[i - 1], (long)c.dcap[i] * K.D[i]});
     c.zcap[i] = (int)std::max<long>(v, 1);
     c.zcap[i] = std::max(c.zcap[i], cur[i]);  // truncate-only pass: z_i = d_i
   }
@@ -653,21 +684,26 @@ qlb_status plan_buffers(qlb_state* st, const Kraus& K) {
   if ((s = realloc_buf(ctx, &st->T2, &t2, nT))) return s;
   if ((s = realloc_buf(ctx, &st->T3, &t3, nT))) return s;
   st->nT = std::max(st->nT, nT);
-  // split-K of the zip-up Grams: their (2 z) x (2 z) outputs make few 32 x 32 tiles
-  // over a long K = d D, so the K range is spread until about 64 CTAs work on it
+  // every GEMM of the step runs on the work-distributed grid with this workspace;
+  // the zip-up Grams take the tuned cap on their K split when the table has one
   st->gram_split.assign(L, 1);
-  size_t nWs = 1;
   for (int i = 0; i + 1 < L; i++) {
     const long mm = 2L * c.zcap[i], kk = (long)c.dcap[i + 1] * D[i + 1];
-    const int ks = gram_splitk(ctx, mm, kk);
-    st->gram_split[i] = ks;
-    if (ks > 1) nWs = std::max(nWs, (size_t)ks * mm * mm);
+    st->gram_split[i] = gram_splitk(ctx, mm, kk);
   }
-  if ((s = realloc_buf(ctx, &st->Wsk, &st->nWsk, nWs))) return s;
+  {
+    zd* before = st->Wsk;
+    if ((s = realloc_buf(ctx, &st->Wsk, &st->nWsk, gemm_workspace_elems(gemm_grid_default())))) return s;
+    if (st->Wsk != before) QLB_CUDA_TRY(cudaMemsetAsync(st->Wsk, 0, sizeof(zd) * st->nWsk, st->stream));
+  }
   size_t new_ew = eig_workspace_elems(n_eig);
+  if (ctx->opt.zip_solver) new_ew = std::max(new_ew, zipqr_workspace_elems(n_eig));
   if ((s = realloc_buf(ctx, &st->eigw, &st->nEw, new_ew))) return s;
   if (!st->d_lam) {
     if ((s = dev_alloc(ctx, (void**)&st->d_lam, sizeof(double) * 1024))) return s;
+  }
+  if (!st->d_gate) {
+    if ((s = dev_alloc(ctx, (void**)&st->d_gate, sizeof(int)))) return s;
   }
   // sites: grow keeping their content
   for (int i = 0; i < L; i++) {
@@ -897,11 +933,7 @@ qlb_status enqueue_step(qlb_state* st, const Kraus& K, bool count_step) {
     g.lda = g.ldb = dvar(SB(i + 1), Dr);
     g.ldc = dvar(ZB(st, i), 2);
     g.m_max = g.n_max = 2 * cap(ZB(st, i));
-    if (i < (int)st->gram_split.size() && st->gram_split[i] > 1 &&
-        (size_t)st->gram_split[i] * g.m_max * g.n_max <= st->nWsk) {
-      g.ksplit = st->gram_split[i];
-      g.ws = st->Wsk;
-    }
+    if (i < (int)st->gram_split.size() && st->gram_split[i] >= 1) g.ksplit = st->gram_split[i];
     if ((s = gemm(st, g))) return s;
     EigDesc e{};
     e.G = st->G;
@@ -911,11 +943,12 @@ qlb_status enqueue_step(qlb_state* st, const Kraus& K, bool count_step) {
     e.out_mode = 0;
     e.dim_out = ZB(st, i + 1);
     e.tol = st->tol * o.zip_tol_factor;
-    e.cap = dconst(std::min(st->chi_max, cap(ZB(st, i + 1))));
+    const int zc = o.zip_chi_max > 0 ? std::max(o.zip_chi_max, st->chi_max) : st->chi_max;
+    e.cap = dconst(std::min(zc, cap(ZB(st, i + 1))));
     e.gap = o.degeneracy_gap;
     e.max_sweeps = o.max_sweeps;
     e.err = st->d_err;
-    if ((s = eig(st, e))) return s;
+    if ((s = zip_range(st, e))) return s;
     // carry C' = U^dag M  -> [k][(r, b)]
     g = gdesc();
     g.kclass = QLB_K_APPLY;

@@ -1,10 +1,11 @@
-// Autotuner of the launch shapes of the step (K11 of the build plan): the split-K
-// factor of the zip-up Gram GEMM G = M M^dag, whose (2z) x (2z) output makes few
-// 32 x 32 tiles over a long K = d D.  For every bucket (rows m, inner size K) the
-// tuner times the GEMM at split factors 1, 2, 4, 8, 16 with CUDA events (best of
-// three, on random data in a scratch allocation) and keeps the fastest; the table
-// lives in the context and can be written to / read from a text file of lines
-// "m K ksplit", so a tuning run on one GPU serves later runs.
+// Autotuner of the launch shapes of the step: the cap on the run-time K split of
+// the zip-up Gram GEMM G = M M^dag, whose (2z) x (2z) output makes few 32 x 32 tiles
+// over a long K = d D (the work-distributed GEMM splits K until its fixed grid is
+// full; more parts mean more partial tiles to add).  For every bucket (rows m,
+// inner size K) the tuner times the GEMM with caps 1, 2, 4, 8, 16 with CUDA events
+// (best of three, on random data in a scratch allocation) and keeps the fastest;
+// the table lives in the context and can be written to / read from a text file of
+// lines "m K ksplit", so a tuning run on one GPU serves later runs.
 
 #include <algorithm>
 #include <cstdio>
@@ -41,8 +42,7 @@ int gram_splitk(const qlb_ctx* ctx, long mm, long kk) {
     auto it = ctx->gram_tune.find({bucket_m(mm), bucket_k(kk)});
     if (it != ctx->gram_tune.end()) return std::max(1, std::min(it->second, (int)std::max<long>(1, kk / 16)));
   }
-  const long tiles = ((mm + 31) / 32) * ((mm + 31) / 32);
-  return (int)std::min<long>({16, std::max<long>(1, 64 / std::max<long>(1, tiles)), std::max<long>(1, kk / 64)});
+  return 0;  // no cap: the kernel's own run-time rule
 }
 
 }  // namespace qlb
@@ -63,7 +63,8 @@ QLB_API qlb_status qlb_autotune(qlb_ctx* ctx, const char* path) {
     cudaFree(W);
   };
   if (cudaMalloc(&M, sizeof(zd) * mmax * kmax) != cudaSuccess || cudaMalloc(&G, sizeof(zd) * mmax * mmax) != cudaSuccess ||
-      cudaMalloc(&W, sizeof(zd) * 16 * mmax * mmax) != cudaSuccess) {
+      cudaMalloc(&W, sizeof(zd) * gemm_workspace_elems(gemm_grid_default())) != cudaSuccess ||
+      cudaMemset(W, 0, sizeof(zd) * gemm_workspace_elems(gemm_grid_default())) != cudaSuccess) {
     cleanup();
     set_error("qlb_autotune: scratch allocation failed");
     return QLB_ENOMEM;

@@ -36,6 +36,7 @@ class qlb_options(C.Structure):
         ("device", C.c_int), ("precision", C.c_int), ("tol", C.c_double), ("chi_max", C.c_int),
         ("chi_mu_max", C.c_int), ("zip_tol_factor", C.c_double), ("degeneracy_gap", C.c_double),
         ("max_sweeps", C.c_int), ("hbm_budget", C.c_size_t), ("stream_ordered", C.c_int),
+        ("zip_solver", C.c_int), ("zip_chi_max", C.c_int), ("mixed_gemm", C.c_int),
     ]
 
 
@@ -77,6 +78,11 @@ _SIGS = {
     "qlb_load_tuning": (_st, [_vp, C.c_char_p]),
     "qlb_tc_zgemm": (_st, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                            C.POINTER(C.c_double)]),
+    "qlb_zgemm_check": (_st, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                              C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "qlb_eig_check": (_st, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.c_double, C.c_int,
+                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int),
+                            C.POINTER(C.c_double)]),
     "qlb_system_create": (_st, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_vp)]),
     "qlb_system_destroy": (None, [_vp]),
     "qlb_op_build": (_st, [_vp, C.POINTER(qlb_term), C.c_int, C.c_double, C.c_int, C.POINTER(_vp)]),
@@ -187,10 +193,13 @@ class Ctx:
         return n.value
 
     def solver_stats(self):
-        out = (C.c_double * 7)()
-        _check(self.lib.qlb_profile_solver_stats(self.h, out, 7))
+        out = (C.c_double * 9)()
+        _check(self.lib.qlb_profile_solver_stats(self.h, out, 9))
+        # global_ws: solves beyond one CTA's shared memory; zip_range: zip-up bonds given
+        # to the pivoted Gram-Schmidt range basis, zip_fallback: of those, the ones that
+        # reached the cap and went to the Jacobi solve
         return dict(solves=out[0], sweeps=out[1], sum_n=out[2], sum_k=out[3], at_limit=out[4],
-                    global_ws=out[5], max_n=out[6])  # global_ws: solves beyond one CTA's shared memory
+                    global_ws=out[5], max_n=out[6], zip_range=out[7], zip_fallback=out[8])
 
     def profile_enable(self, on=True):
         _check(self.lib.qlb_profile_enable(self.h, int(on)))
@@ -436,6 +445,44 @@ def qlb_tc_zgemm(device: int, A, B) -> np.ndarray:
     _check(load().qlb_tc_zgemm(int(device), m, n, k, A.ctypes.data_as(dp), B.ctypes.data_as(dp),
                                Cm.ctypes.data_as(dp)))
     return Cm
+
+
+GEMM_FP64, GEMM_DF64, GEMM_TC = range(3)
+
+
+def qlb_zgemm_check(device: int, engine: int, A, B):
+    """A @ B (complex128) through one of the step's GEMM engines; returns (C, device ms)."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.complex128))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.complex128))
+    m, k = A.shape
+    k2, n = B.shape
+    assert k == k2
+    Cm = np.zeros((m, n), dtype=np.complex128)
+    ms = C.c_double()
+    dp = C.POINTER(C.c_double)
+    _check(load().qlb_zgemm_check(int(device), int(engine), m, n, k, A.ctypes.data_as(dp), B.ctypes.data_as(dp),
+                                  Cm.ctypes.data_as(dp), C.byref(ms)))
+    return Cm, ms.value
+
+
+SOLVER_STEP, SOLVER_JACOBI, SOLVER_CLUSTER8, SOLVER_CLUSTER16, SOLVER_QL, SOLVER_RANGE = range(6)
+
+
+def qlb_eig_check(device: int, precision: int, solver: int, G, tol: float = 0.0, cap: int = 0):
+    """One truncation solve of the Hermitian matrix G by the named kernel.  Returns
+    (eigenvalues descending, kept vectors n x k or None, k, device ms); k = -1 when
+    the range basis (SOLVER_RANGE) reached the cap first."""
+    G = np.ascontiguousarray(np.asarray(G, dtype=np.complex128))
+    n = G.shape[0]
+    lam = np.zeros(n)
+    V = np.zeros(n * n, dtype=np.complex128)
+    k, ms = C.c_int(), C.c_double()
+    dp = C.POINTER(C.c_double)
+    _check(load().qlb_eig_check(int(device), int(precision), int(solver), n, G.ctypes.data_as(dp), float(tol),
+                                int(cap or n), lam.ctypes.data_as(dp), V.ctypes.data_as(dp), C.byref(k),
+                                C.byref(ms)))
+    kk = k.value
+    return lam, (V[:n * kk].reshape(n, kk) if kk > 0 else None), kk, ms.value
 
 
 class Server:
