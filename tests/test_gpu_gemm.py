@@ -4,8 +4,11 @@ CTA of each tile), the same GEMM in double-float (the mixed forms) and the
 tensor-core 3xTF32 GEMM, against numpy's complex128 product.
 
 Bars (relative Frobenius error of C): FP64 8 eps sqrt(k), double-float 2^-44
-sqrt(k) (a ~48-bit significand per operation), tensor cores 2e-5 (3xTF32 with
-FP32 accumulation).  Shapes cover a single tile, ragged edges, the split path
+sqrt(k) (a ~48-bit significand per operation).  Tensor cores, per entry: 3xTF32
+keeps ~21 bits of each operand (2^-19 for the products) and every one of the 2k
+real additions into the FP32 accumulator in tensor memory may lose up to 2^-23 of
+the running sum (the accumulation is not round-to-nearest, so these losses add up
+with K instead of averaging out): |C - AB| <= (2^-19 + 2k 2^-23) |A| |B|.  Shapes cover a single tile, ragged edges, the split path
 (few tiles over a long K), many tiles (no split) and K = 0."""
 import numpy as np
 import pytest
@@ -34,9 +37,13 @@ def test_engine_against_numpy(engine, m, n, k):
     if k == 0:
         assert np.all(C == 0)
         return
-    err = np.linalg.norm(C - ref) / np.linalg.norm(ref)
-    bar = {Q.GEMM_FP64: 8 * 2.2e-16 * np.sqrt(k), Q.GEMM_DF64: 2.0 ** -44 * np.sqrt(k), Q.GEMM_TC: 2e-5}[engine]
-    assert err < bar, (err, bar)
+    if engine == Q.GEMM_TC:
+        bound = (2.0 ** -19 + 2 * k * 2.0 ** -23) * (np.abs(A) @ np.abs(B))
+        assert np.all(np.abs(C - ref) <= bound), np.max(np.abs(C - ref) / bound)
+    else:
+        err = np.linalg.norm(C - ref) / np.linalg.norm(ref)
+        bar = {Q.GEMM_FP64: 8 * 2.2e-16 * np.sqrt(k), Q.GEMM_DF64: 2.0 ** -44 * np.sqrt(k)}[engine]
+        assert err < bar, (err, bar)
     assert ms > 0
 
 
