@@ -423,15 +423,44 @@ def run_other_workload(args):
     for st in states:
         st.step(dt, args.warmup)
     ctx.synchronize()
+    snaps = [st.export() for st in states]
+    ctx.profile_reset()
+    torch.cuda.synchronize()
+    # each state on its own stream (its own CUDA graph per state)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for st in states:
+            st.step(dt, 1)  # enqueued on each state's own stream
+    ctx.synchronize()
+    wall_streams = time.perf_counter() - t0
+    per_stream_end = [st.bond_dims() for st in states]
+    # the same steps again from the same snapshots as one group (one launch per
+    # phase of the step over all states)
+    for st, sn in zip(states, snaps):
+        st.import_(sn)
+    grp = qlb.Group(ctx, states) if len(states) > 1 else None
+    if grp is not None:
+        grp.step(dt, 1)  # records and captures the group's graph
+        ctx.synchronize()
+        for st, sn in zip(states, snaps):
+            st.import_(sn)
+        ctx.synchronize()
     ctx.profile_reset()
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            for st in states:
-                st.step(dt, 1)  # enqueued on each state's own stream
+        if grp is not None:
+            for _ in range(args.steps):
+                grp.step(dt, 1)
+        else:
+            for _ in range(args.steps):
+                states[0].step(dt, 1)
         ctx.synchronize()
         wall = time.perf_counter() - t0
+    same_as_streams = [st.bond_dims() for st in states] == per_stream_end
+    launches = grp.launches() if grp is not None else None
+    if grp is not None:
+        grp.close()
     sv = ctx.solver_stats()
     ns = max(1.0, sv["solves"])
     value = len(states) * args.steps / wall
@@ -442,7 +471,13 @@ def run_other_workload(args):
             "config": {"workload": args.workload, "R": cfg["R"], "dt": dt, "chi_max": cfg["chi_max"],
                        "chi_mu_max": cfg["chi_mu_max"], "tol": cfg["tol"], "states": len(states),
                        "bonds_after": [st.bond_dims() for st in states[:2]],
-                       "timing": "host wall clock around K steps of every state, device synchronised"},
+                       "timing": "host wall clock around K steps of every state, device synchronised",
+                       "engine": "group (one launch per phase over all states)" if grp is not None
+                       else "single state, CUDA graph"},
+            "per_stream": {"value": len(states) * args.steps / wall_streams,
+                           "ms_per_step": 1e3 * wall_streams / args.steps,
+                           "engine": "one CUDA graph per state, each on its own stream"},
+            "group_launches_per_step": launches, "group_same_bonds_as_streams": same_as_streams,
             "solver": {"solves_per_step": sv["solves"] / (args.steps * len(states)), "mean_n": sv["sum_n"] / ns,
                        "max_n": sv["max_n"], "sweeps_per_solve": sv["sweeps"] / ns},
             "clocks": clk.summary()}

@@ -273,6 +273,37 @@ qlb_status qlb_kraus_to_dense(qlb_state* st, double dt, int k, double* out, size
 qlb_status qlb_state_export(qlb_state* st, void* out, size_t cap, size_t* n_bytes);
 qlb_status qlb_state_import(qlb_state* st, const void* in, size_t n_bytes);
 
+/* ------------------------------------------------------------------ groups */
+
+/* Many independent states stepped together.  The method's step (Sec. V.B with
+ * the zip-up of Sec. V.A and the purification truncation of Sec. IV.A) is a chain
+ * of small dependent launches per state: apart, one state keeps only a few SMs
+ * busy.  A group runs each launch of the step once for all of its members (one
+ * CTA, cluster or GEMM grid slice per member, blockIdx.y = member), captured as
+ * one CUDA graph on the group's own stream, so n_states states cost one chain of
+ * launches.  A member's numbers are the ones its own qlb_step computes: the same
+ * kernels, shapes, K splits and reduction orders (results equal bit for bit when
+ * the members share one planned shape).
+ *
+ * The members must belong to ctx, be distinct, and step the same launch sequence:
+ * the same number of sites, the same precision form and Kraus scheme (their mode
+ * sizes, operators, caps and bond dimensions may differ; each is planned for its
+ * own).  The group holds the handles, not their ownership: destroy the group
+ * before any of its states.  Between group steps the members stay usable one by
+ * one (observables, qlb_step, qlb_truncate); their own streams are ordered before
+ * and after the group's work.  n_states in 1..4096. */
+typedef struct qlb_group qlb_group;
+qlb_status qlb_group_create(qlb_ctx* ctx, qlb_state* const* states, int n_states, qlb_group** out);
+void qlb_group_destroy(qlb_group* g);
+/* n steps of size dt for every member (qlb_step's semantics and return codes;
+ * QLB_WUNSTABLE if any member's map is unstable at dt; the first member error
+ * otherwise).  Synchronous unless the context is stream_ordered. */
+qlb_status qlb_group_step(qlb_group* g, double dt, int64_t n);
+/* Kernel launches of one captured group step (0 before the first step). */
+qlb_status qlb_group_launches(qlb_group* g, int* per_step);
+/* The cudaStream_t the group's steps run on. */
+qlb_status qlb_group_stream(qlb_group* g, void** stream);
+
 /* ------------------------------------------------------------------ serving */
 
 /* Continuous-batching service of independent solves on one GPU (the serving
@@ -282,11 +313,13 @@ qlb_status qlb_state_import(qlb_state* st, const void* in, size_t n_bytes);
  * its systems or states meanwhile).  The worker admits pending requests in
  * arrival order while fewer than max_live are running and the request's
  * estimated device memory fits hbm_budget (0: no limit) next to the running ones;
- * it builds the request's system and state, steps every running state in chunks
- * of `chunk` steps on the state's own stream (the chunks of different requests
- * overlap on the GPU), evaluates the request's observables when its steps are
- * done, and releases its memory and slot.  The context must be created with
- * stream_ordered = 1. */
+ * it builds the request's system and state, and steps the running states in
+ * chunks of at most `chunk` steps: running requests whose step plans have the
+ * same shape (sites, precision form, Kraus MPO bonds, bond capacities) step
+ * together as one group (see "groups"), each group on its own stream, so the
+ * groups overlap on the GPU.  It evaluates a request's observables when its
+ * steps are done, and releases its memory and slot.  The context must be created
+ * with stream_ordered = 1. */
 typedef struct qlb_server qlb_server;
 
 /* One solve.  Every array is copied at qlb_submit (dense factors included). */

@@ -43,6 +43,13 @@ int gram_splitk(const qlb_ctx* ctx, long m, long K);
 // is set when a bounded wait of the kernel gave up
 cudaError_t launch_gemm_tc(const GemmDesc& g, const int* d_dims, cudaStream_t s, int* err, double* prof);
 size_t tc_gemm_smem_bytes();
+// grouped launches: the same launch of S states at once (blockIdx.y = member), the
+// member descriptors in device memory (d_grp[S]); n_max = the largest planned size
+cudaError_t launch_gemm_group(const GemmDesc* d_grp, int S, int use_df, cudaStream_t s, double* prof);
+template <typename R>
+cudaError_t launch_eig_group(int n_max, const EigDesc* d_grp, int S, cudaStream_t s, double* prof);
+template <typename R>
+cudaError_t launch_zipqr_group(int n_max, const EigDesc* d_grp, int S, cudaStream_t s, double* prof);
 void init_tc_attributes();
 
 qlb_status svd_osj(qlb_ctx* ctx, zd* X, int m, int n, double tol, int cap, zd** U, int u_scale, zd** Rr,

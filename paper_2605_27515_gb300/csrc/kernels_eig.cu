@@ -162,10 +162,15 @@ __device__ void eig_finish(const EigDesc& e, int* d, int n, const double* lam, c
   }
 }
 
-template <typename R, int NT>
+template <typename R, int NT, bool GRP = false>
 __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R>* work, int dyn_bytes,
-                                           double* prof) {
+                                           double* prof, const EigDesc* __restrict__ grp) {
   extern __shared__ unsigned char smem_raw[];
+  if constexpr (GRP) {  // grouped launch: one CTA per member (blockIdx.y)
+    e = grp[blockIdx.y];
+    d = e.dims;
+    work = (cx<R>*)e.work;
+  }
   if (e.gate && *e.gate == 0) return;  // the zip-up range basis already served this bond
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
@@ -376,11 +381,16 @@ struct JRot {
 
 constexpr int EIG_CL_MAX_NP = 256;
 
-template <typename R, int NT, int C>
-__global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, double* prof) {
+template <typename R, int NT, int C, bool GRP = false>
+__global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, double* prof,
+                                              const EigDesc* __restrict__ grp) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ unsigned char smem_raw[];
+  if constexpr (GRP) {  // grouped launch: one cluster per member (blockIdx.y; the cluster spans x)
+    e = grp[blockIdx.y];
+    d = e.dims;
+  }
   if (e.gate && *e.gate == 0) return;  // the zip-up range basis already served this bond
   const int n = dev_eval(e.n, d);
   const int tid = threadIdx.x;
@@ -956,12 +966,13 @@ size_t eig_workspace_elems(int n_max) {
 }
 
 template <typename R, int C>
-cudaError_t launch_eig_cl(const EigDesc& e, const int* d_dims, cudaStream_t s, double* prof) {
+cudaError_t launch_eig_cl(const EigDesc& e, const int* d_dims, cudaStream_t s, double* prof,
+                          const EigDesc* grp = nullptr, int S = 1) {
   const int np = e.n_max + (e.n_max & 1);
   const int rpb = (np + C - 1) / C;
   size_t dyn = 3 * (size_t)rpb * np * sizeof(cx<R>);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(C, 1, 1);
+  cfg.gridDim = dim3(C, S, 1);
   cfg.blockDim = dim3(256, 1, 1);
   cfg.dynamicSmemBytes = dyn;
   cfg.stream = s;
@@ -972,7 +983,8 @@ cudaError_t launch_eig_cl(const EigDesc& e, const int* d_dims, cudaStream_t s, d
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_eig_cl<R, 256, C>, e, (int*)d_dims, prof);
+  if (grp) return cudaLaunchKernelEx(&cfg, k_eig_cl<R, 256, C, true>, e, (int*)d_dims, prof, grp);
+  return cudaLaunchKernelEx(&cfg, k_eig_cl<R, 256, C, false>, e, (int*)d_dims, prof, grp);
 }
 
 template <typename R>
@@ -995,15 +1007,41 @@ cudaError_t launch_eig(const EigDesc& e, const int* d_dims, cudaStream_t s, void
   // chains per rotation, so a full CTA of warps hides their latency.
   constexpr bool wide = std::is_same<R, df64>::value;
   if (e.n_max <= 24)
-    k_eig<R, 128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+    k_eig<R, 128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, nullptr);
   else if (wide)
-    k_eig<R, 1024><<<1, 1024, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+    k_eig<R, 1024><<<1, 1024, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, nullptr);
   else
-    k_eig<R, 512><<<1, 512, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+    k_eig<R, 512><<<1, 512, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, nullptr);
   return cudaGetLastError();
 }
 template cudaError_t launch_eig<double>(const EigDesc&, const int*, cudaStream_t, void*, double*);
 template cudaError_t launch_eig<df64>(const EigDesc&, const int*, cudaStream_t, void*, double*);
+
+// The eigen-solves of S states in one launch, with the kernel launch_eig picks for
+// the largest planned size n_max over the members (every kernel takes any runtime
+// size up to its planned one): one CTA, or one cluster, per member (blockIdx.y).
+template <typename R>
+cudaError_t launch_eig_group(int n_max, const EigDesc* d_grp, int S, cudaStream_t s, double* prof) {
+  if (S <= 0) return cudaSuccess;
+  EigDesc e{};
+  e.n_max = n_max;
+  if (n_max > 24 && n_max <= EIG_CL_MAX_NP) {
+    if (n_max <= 128) return launch_eig_cl<R, 8>(e, nullptr, s, prof, d_grp, S);
+    return launch_eig_cl<R, 16>(e, nullptr, s, prof, d_grp, S);
+  }
+  size_t want = eig_smem_bytes<R>(n_max);
+  int dyn = (int)(want <= EIG_SMEM_LIMIT ? want : EIG_SMEM_LIMIT);
+  constexpr bool wide = std::is_same<R, df64>::value;
+  if (n_max <= 24)
+    k_eig<R, 128, true><<<dim3(1, S), 128, dyn, s>>>(e, nullptr, nullptr, dyn, prof, d_grp);
+  else if (wide)
+    k_eig<R, 1024, true><<<dim3(1, S), 1024, dyn, s>>>(e, nullptr, nullptr, dyn, prof, d_grp);
+  else
+    k_eig<R, 512, true><<<dim3(1, S), 512, dyn, s>>>(e, nullptr, nullptr, dyn, prof, d_grp);
+  return cudaGetLastError();
+}
+template cudaError_t launch_eig_group<double>(int, const EigDesc*, int, cudaStream_t, double*);
+template cudaError_t launch_eig_group<df64>(int, const EigDesc*, int, cudaStream_t, double*);
 
 // One named solver regardless of the size rule above (the check entry point):
 // 1 one-CTA Jacobi, 2 cluster Jacobi over 8 CTAs (n <= 128), 3 over 16 CTAs
@@ -1023,11 +1061,11 @@ cudaError_t launch_eig_kind(int kind, const EigDesc& e, const int* d_dims, cudaS
     size_t want = eig_smem_bytes<R>(e.n_max);
     int dyn = (int)(want <= EIG_SMEM_LIMIT ? want : EIG_SMEM_LIMIT);
     if (e.n_max <= 24)
-      k_eig<R, 128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+      k_eig<R, 128><<<1, 128, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, nullptr);
     else if (std::is_same<R, df64>::value)
-      k_eig<R, 1024><<<1, 1024, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+      k_eig<R, 1024><<<1, 1024, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, nullptr);
     else
-      k_eig<R, 512><<<1, 512, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+      k_eig<R, 512><<<1, 512, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, nullptr);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
@@ -1036,6 +1074,19 @@ template cudaError_t launch_eig_kind<double>(int, const EigDesc&, const int*, cu
 template cudaError_t launch_eig_kind<df64>(int, const EigDesc&, const int*, cudaStream_t, void*, double*);
 
 void init_kernel_attributes() {
+  cudaFuncSetAttribute(k_eig<double, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig<double, 512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig<df64, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig<df64, 1024, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig_cl<double, 256, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig_cl<double, 256, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig_cl<double, 256, 16, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(k_eig_cl<df64, 256, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig_cl<df64, 256, 16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)EIG_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_eig_cl<df64, 256, 16, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   set_attr<double, 128>();
   set_attr<double, 256>();
   set_attr<double, 512>();

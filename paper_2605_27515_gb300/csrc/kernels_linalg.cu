@@ -79,8 +79,16 @@ __device__ __forceinline__ cx<R> gemm_alpha(const GemmDesc& g) {
 
 // R: the storage type of A, B, C; Cm: the type the products are formed and summed in
 // (R itself, or double-float for FP64 storage in the mixed forms)
-template <typename R, typename Cm>
-__global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc g, const int* __restrict__ d, double* prof) {
+template <typename R, typename Cm, bool GRP>
+__global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc g, const int* __restrict__ d, double* prof,
+                                                    const GemmDesc* __restrict__ grp) {
+  // grouped launch: this CTA works on member blockIdx.y, whose descriptor (and dims)
+  // come from the group's table; the K split is decided on the member's nominal grid
+  if constexpr (GRP) {
+    g = grp[blockIdx.y];
+    d = g.dims;
+  }
+  const int gnom = g.split_grid > 0 ? g.split_grid : (int)gridDim.x;
   const int m = dev_eval(g.m, d), n = dev_eval(g.n, d), K = dev_eval(g.k, d);
   const int nb1 = dev_eval(g.nb1, d), nb2 = dev_eval(g.nb2, d);
   const int nb = nb1 * nb2;
@@ -89,9 +97,9 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc g, const int* __res
   const long ntiles = (long)tm * tn * nb;
   // the K split of this launch, from the run-time sizes (the same in every CTA)
   int ks = 1;
-  if (g.ws && K > GB_K && ntiles < (long)gridDim.x) {
+  if (g.ws && K > GB_K && ntiles < (long)gnom) {
     const int cap = g.ksplit >= 1 ? g.ksplit : GB_SPLIT_CAP;
-    ks = (int)min((long)cap, (long)gridDim.x / ntiles);
+    ks = (int)min((long)cap, (long)gnom / ntiles);
     ks = min(ks, (K + GB_K - 1) / GB_K);
     if (ks < 1) ks = 1;
   }
@@ -103,7 +111,7 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc g, const int* __res
   }
   const long lda = dev_eval(g.lda, d), ldb = dev_eval(g.ldb, d), ldc = dev_eval(g.ldc, d);
   cx<Cm>* part_ws = (cx<Cm>*)g.ws;
-  int* counters = g.ws ? (int*)(part_ws + (long)gridDim.x * GB_TILE) : nullptr;
+  int* counters = g.ws ? (int*)(part_ws + (long)gnom * GB_TILE) : nullptr;
 
   __shared__ cx<Cm> As[GB_K][GB_M + 1];
   __shared__ cx<Cm> Bs[GB_K][GB_N + 1];
@@ -250,17 +258,35 @@ cudaError_t launch_gemm(const GemmDesc& g, const int* d_dims, cudaStream_t s, do
   const int grid = g.ws ? (g.grid > 0 ? g.grid : gemm_grid_default()) : (int)std::min<long>(planned, 4096);
   GemmDesc gg = g;
   if (!g.ws) gg.ksplit = 1;
+  gg.split_grid = 0;
   if constexpr (std::is_same<R, double>::value) {
     if (g.df64) {
-      k_gemm<R, df64><<<grid, G_THREADS, 0, s>>>(gg, d_dims, prof);
+      k_gemm<R, df64, false><<<grid, G_THREADS, 0, s>>>(gg, d_dims, prof, nullptr);
       return cudaGetLastError();
     }
   }
-  k_gemm<R, R><<<grid, G_THREADS, 0, s>>>(gg, d_dims, prof);
+  k_gemm<R, R, false><<<grid, G_THREADS, 0, s>>>(gg, d_dims, prof, nullptr);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_gemm<double>(const GemmDesc&, const int*, cudaStream_t, double*);
 template cudaError_t launch_gemm<float>(const GemmDesc&, const int*, cudaStream_t, double*);
+
+// The same GEMM of S states in one launch: grid (per-member CTAs, S).  Every member
+// descriptor in d_grp carries its dims, a workspace for the default grid and
+// split_grid = the default grid, so each member is split and summed exactly as in
+// its own launch; the per-member CTA count only changes how the work items are
+// shared out (S x per-member CTAs ~ two per SM over the whole group).
+cudaError_t launch_gemm_group(const GemmDesc* d_grp, int S, int use_df, cudaStream_t s, double* prof) {
+  if (S <= 0) return cudaSuccess;
+  const int full = gemm_grid_default();
+  const int per = std::max(8, std::min(full, (full + S - 1) / S));
+  GemmDesc dummy{};
+  if (use_df)
+    k_gemm<double, df64, true><<<dim3(per, S), G_THREADS, 0, s>>>(dummy, nullptr, prof, d_grp);
+  else
+    k_gemm<double, double, true><<<dim3(per, S), G_THREADS, 0, s>>>(dummy, nullptr, prof, d_grp);
+  return cudaGetLastError();
+}
 
 }  // namespace qlb

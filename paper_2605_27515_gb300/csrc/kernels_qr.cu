@@ -169,10 +169,15 @@ __device__ __forceinline__ R cta_sum(R v, R* slot) {
   return s;
 }
 
-template <typename R>
+template <typename R, bool GRP = false>
 __global__ void __launch_bounds__(QR_NT) k_zipqr(EigDesc e, int* __restrict__ d, cx<R>* work, int dyn_bytes,
-                                                  double* prof) {
+                                                  double* prof, const EigDesc* __restrict__ grp) {
   extern __shared__ unsigned char smem_raw[];
+  if constexpr (GRP) {  // grouped launch: one CTA per member (blockIdx.y)
+    e = grp[blockIdx.y];
+    d = e.dims;
+    work = (cx<R>*)e.work;
+  }
   __shared__ cx<R> s_c[QR_MAX_N];       // re-orthogonalisation coefficients q_i^dag w_p
   __shared__ cx<R> s_part[QR_NT];       // partial sums of sum_i c_i q_i[row]
   __shared__ int s_q[QR_MAX_N];         // column slot of q_j
@@ -364,11 +369,25 @@ template <typename R>
 cudaError_t launch_zipqr(const EigDesc& e, const int* d_dims, cudaStream_t s, void* work, double* prof) {
   const size_t want = (size_t)e.n_max * e.n_max * sizeof(cx<R>);
   const int dyn = (int)(want <= QR_SMEM_LIMIT ? want : QR_SMEM_LIMIT);
-  k_zipqr<R><<<1, QR_NT, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof);
+  k_zipqr<R><<<1, QR_NT, dyn, s>>>(e, (int*)d_dims, (cx<R>*)work, dyn, prof, nullptr);
   return cudaGetLastError();
 }
 template cudaError_t launch_zipqr<double>(const EigDesc&, const int*, cudaStream_t, void*, double*);
 template cudaError_t launch_zipqr<df64>(const EigDesc&, const int*, cudaStream_t, void*, double*);
+
+// The range bases of S states' zip-up bonds in one launch (one CTA per member);
+// n_max is the largest planned size over the members.
+template <typename R>
+cudaError_t launch_zipqr_group(int n_max, const EigDesc* d_grp, int S, cudaStream_t s, double* prof) {
+  if (S <= 0) return cudaSuccess;
+  const size_t want = (size_t)n_max * n_max * sizeof(cx<R>);
+  const int dyn = (int)(want <= QR_SMEM_LIMIT ? want : QR_SMEM_LIMIT);
+  EigDesc dummy{};
+  k_zipqr<R, true><<<dim3(1, S), QR_NT, dyn, s>>>(dummy, nullptr, nullptr, dyn, prof, d_grp);
+  return cudaGetLastError();
+}
+template cudaError_t launch_zipqr_group<double>(int, const EigDesc*, int, cudaStream_t, double*);
+template cudaError_t launch_zipqr_group<df64>(int, const EigDesc*, int, cudaStream_t, double*);
 
 cudaError_t launch_solver(bool mixed, int solver, const EigDesc& e, const int* d_dims, cudaStream_t s, void* work) {
   if (solver == 5)
@@ -382,6 +401,8 @@ cudaError_t launch_solver(bool mixed, int solver, const EigDesc& e, const int* d
 void init_qr_attributes() {
   cudaFuncSetAttribute(k_zipqr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QR_SMEM_LIMIT);
   cudaFuncSetAttribute(k_zipqr<df64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QR_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_zipqr<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QR_SMEM_LIMIT);
+  cudaFuncSetAttribute(k_zipqr<df64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)QR_SMEM_LIMIT);
 }
 
 }  // namespace qlb

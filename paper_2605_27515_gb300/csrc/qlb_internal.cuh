@@ -123,6 +123,12 @@ struct GemmDesc {
   // 1: FP64 operands multiplied and summed in double-float (~48-bit significands) on
   // the FP32 pipes; the result is stored in FP64
   int df64;
+  // Grouped launches (one launch over the same GEMM of several states, blockIdx.y
+  // = member): the member's dims array, and the grid that decides the K split and
+  // the workspace layout (so that a member gets the split, and the bits, it gets
+  // when launched alone on the full grid); 0: gridDim.x
+  const int* dims;
+  int split_grid;
 };
 
 // Hermitian eigen solve + truncation select (one CTA per problem).
@@ -149,6 +155,9 @@ struct EigDesc {
   double* solver_stats; // optional counters (see qlb_ctx::d_solver)
   int* gate;            // optional: when set, the eigen-solve runs only if *gate != 0
                         // (the zip-up range basis sets it when its cap was reached)
+  // grouped launches (blockIdx.y = member): the member's dims array and workspace
+  int* dims;
+  void* work;
 };
 
 // ------------------------------------------------------------------ error plumbing

@@ -122,6 +122,50 @@ struct Kraus {
   ~Kraus();
 };
 
+// Arguments of the small launches of a step (also the rows of a group's table).
+struct StepBeginArgs {
+  int* d;
+  int L, B;
+  zd* C0;
+  long c0_cap;
+  zd* W0;
+  const zd* h1c0;
+  int D1tot, drive_off, drive_D1;
+  const double* f;
+  long long n_f;
+  const long long* step;
+  double dt;
+  double* stats;
+};
+struct StepEndArgs {
+  long long* step;
+  int count;
+};
+struct CopyArgs {
+  zd* dst;
+  const zd* src;
+  DimExpr cnt;
+  const int* d;
+};
+
+// One launch of a step as recorded (instead of launched) when the state steps as
+// a member of a group: the group launches each position of its members' records
+// once, over all members.
+enum RecKind { REC_BEGIN = 0, REC_END, REC_GEMM, REC_GEMM_TC, REC_ZIPQR, REC_EIG, REC_COPY };
+struct LaunchRec {
+  int kind = 0;
+  int df = 0;        // ZIPQR / EIG: double-float (mixed forms); GEMM: the df64 flag
+  int kclass = 0;    // profiling class
+  long grid_n = 0;   // BEGIN / COPY: elements the launch covers at most
+  GemmDesc g{};
+  EigDesc e{};
+  CopyArgs c{};
+  StepBeginArgs b{};
+  StepEndArgs x{};
+  int* err = nullptr;  // GEMM_TC: the member's error flags
+  const int* dims = nullptr;
+};
+
 }  // namespace qlb
 
 struct qlb_state {
@@ -164,6 +208,8 @@ struct qlb_state {
   int plan_key = 0;     // bumped whenever buffers, caps or the Kraus MPO change
   cudaGraphExec_t graph = nullptr;
   int graph_key = -1;
+  // set while the state's step is recorded for a group (launches go here instead)
+  std::vector<qlb::LaunchRec>* rec = nullptr;
   std::vector<qlb::DevBuf> extra;  // other owned buffers
   ~qlb_state();
 };

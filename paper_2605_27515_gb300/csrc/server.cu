@@ -12,13 +12,16 @@
 //   qlb_cancel  marks a request; the worker drops it between two chunks.
 // The worker admits pending requests in arrival order while a live slot is free
 // and the request's estimated device memory fits the budget next to the live
-// ones; it builds the request's system and state (each state steps on its own
-// CUDA stream), keeps every live state busy with chunks of steps (enqueued
-// without host synchronisation, so the chunks of different requests overlap on
-// the GPU), and when a state has taken all its steps it evaluates the requested
-// observables, releases the state's memory and slot, and admits the next
-// arrival.  A request's result does not depend on the other requests in flight:
-// every state has its own buffers and stream.
+// ones; it builds the request's system and state and plans its step.  Live
+// requests whose plans have the same shape (sites, precision form, Kraus MPO
+// bonds, bond capacities) form a bucket, and a bucket steps its idle members
+// together as a group (one launch per phase of the step over all of them, on the
+// bucket's stream, enqueued without host synchronisation, so the buckets overlap
+// on the GPU), in chunks of at most `chunk` steps.  When a state has taken all
+// its steps the worker evaluates the requested observables, releases the state's
+// memory and slot, and admits the next arrival.  A request's result does not
+// depend on the other requests in flight: every state has its own buffers, and a
+// group member computes bit for bit what it computes alone.
 
 #include <atomic>
 #include <chrono>
@@ -29,6 +32,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <algorithm>
 #include <thread>
 #include <vector>
 
@@ -91,6 +95,7 @@ struct Job {
   std::string error;
   qlb_status status = QLB_OK;
   // device objects (worker thread only)
+  std::string bucket;  // planned shape: requests with equal keys step as one group
   qlb_system* sys = nullptr;
   std::vector<qlb_op*> ops;
   std::vector<qlb_op*> obs_ops;
@@ -102,6 +107,16 @@ struct Job {
 
 using namespace qlb;
 
+// The live requests of one planned shape (sites, precision form, Kraus MPO bonds
+// and bond capacities) step together as a group: one launch per phase of the step
+// over all of them, on the bucket's own stream.
+struct Bucket {
+  qlb::GroupExec exec;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::vector<std::shared_ptr<qlb::Job>> running;  // members of the chunk in flight
+};
+
 struct qlb_server {
   qlb_ctx* ctx = nullptr;
   size_t budget = 0;
@@ -111,6 +126,7 @@ struct qlb_server {
   std::map<int64_t, std::shared_ptr<Job>> jobs;
   std::deque<std::shared_ptr<Job>> pending;
   std::vector<std::shared_ptr<Job>> live;
+  std::map<std::string, Bucket> buckets;  // worker thread only
   int64_t next_ticket = 1;
   size_t used = 0;
   std::atomic<bool> stop{false};
@@ -178,6 +194,13 @@ qlb_status build_job(qlb_ctx* ctx, Job& j) {
   // the step plan (Kraus MPO and buffers) is made once, before the first chunk
   if ((s = build_kraus(j.st, j.dt))) return s;
   if ((s = plan_buffers(j.st, j.st->kraus))) return s;
+  // requests whose plans have the same shape share a group (and so its launches):
+  // the same kernels, grids and K splits as each would get alone
+  std::string key = std::to_string(j.st->L) + "|" + std::to_string(j.st->prec) + "|" + std::to_string(j.sys->order);
+  for (int v : j.st->kraus.D) key += "," + std::to_string(v);
+  key += "|";
+  for (int v : j.st->cap_state) key += "," + std::to_string(v);
+  j.bucket = key;
   return QLB_OK;
 }
 
@@ -270,45 +293,94 @@ void qlb_server::run() {
       progressed = true;
     }
     if (ctx->mem_held > peak_bytes) peak_bytes = ctx->mem_held;
-    for (size_t i = 0; i < live.size();) {
-      auto& j = live[i];
-      cudaError_t q = cudaStreamQuery(j->st->stream);
+    // a bucket whose chunk has finished takes its next one
+    for (auto& kv : buckets) {
+      Bucket& b = kv.second;
+      if (b.running.empty()) continue;
+      cudaError_t q = cudaStreamQuery(b.stream);
       if (q == cudaErrorNotReady) {
         cudaGetLastError();
-        i++;
         continue;
       }
+      b.running.clear();
+    }
+    std::map<std::string, std::vector<std::shared_ptr<Job>>> ready;
+    for (size_t i = 0; i < live.size();) {
+      auto& j = live[i];
+      auto bit = buckets.find(j->bucket);
+      if (bit != buckets.end() && !bit->second.running.empty()) {
+        i++;  // its bucket's chunk is still in flight
+        continue;
+      }
+      if (j->cancel || j->remaining <= 0) {
+        progressed = true;
+        finish(j, !j->cancel);
+        live.erase(live.begin() + i);
+        n_live = (int)live.size();
+        continue;
+      }
+      ready[j->bucket].push_back(j);
+      i++;
+    }
+    for (auto& kv : ready) {
+      auto& js = kv.second;
+      Bucket& b = buckets[kv.first];
+      b.exec.ctx = ctx;
+      qlb_status s = QLB_OK;
+      if (!b.stream && (cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess)) {
+        set_error("bucket stream creation failed");
+        s = QLB_EDEVICE;
+      }
+      int64_t n = chunk;
+      std::vector<qlb_state*> ms;
+      for (auto& j : js) {
+        n = std::min<int64_t>(n, j->remaining);
+        ms.push_back(j->st);
+      }
+      if (s == QLB_OK) s = group_run(b.exec, ms, b.stream, b.ev, n, false);  // enqueued, no wait
       progressed = true;
-      if (j->cancel) {
-        finish(j, false);
-        live.erase(live.begin() + i);
+      if (s < 0) {
+        const std::string msg = get_error();
+        for (auto& j : js) {
+          j->status = s;
+          j->error = msg;
+          finish(j, false);
+          live.erase(std::find(live.begin(), live.end(), j));
+        }
         n_live = (int)live.size();
         continue;
       }
-      if (j->remaining > 0) {
-        const int64_t n = std::min<int64_t>(chunk, j->remaining);
-        qlb_status s = run_steps(j->st, n, false);  // enqueued on the state's stream
-        if (s < 0) {
-          j->status = s;
-          j->error = get_error();
-          finish(j, false);
-          live.erase(live.begin() + i);
-          n_live = (int)live.size();
-          continue;
-        }
-        j->remaining -= n;
-        steps_done += n;
-        i++;
-      } else {
-        finish(j, true);
-        live.erase(live.begin() + i);
-        n_live = (int)live.size();
+      for (auto& j : js) j->remaining -= n;
+      steps_done += n * (int64_t)js.size();
+      b.running = js;
+    }
+    // buckets without live requests give back their graph and table
+    for (auto it = buckets.begin(); it != buckets.end();) {
+      bool used = !it->second.running.empty();
+      for (auto& j : live) used = used || j->bucket == it->first;
+      if (used) {
+        ++it;
+        continue;
       }
+      if (it->second.stream) cudaStreamSynchronize(it->second.stream);
+      it->second.exec.release();
+      if (it->second.ev) cudaEventDestroy(it->second.ev);
+      if (it->second.stream) cudaStreamDestroy(it->second.stream);
+      it = buckets.erase(it);
     }
     if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(100));
   }
+  for (auto& kv : buckets)
+    if (kv.second.stream) cudaStreamSynchronize(kv.second.stream);
   for (auto& j : live) finish(j, false);
   live.clear();
+  for (auto& kv : buckets) {
+    kv.second.exec.release();
+    if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+    if (kv.second.stream) cudaStreamDestroy(kv.second.stream);
+  }
+  buckets.clear();
 }
 
 #define CHECK_ARG(cond, msg) \

@@ -32,41 +32,48 @@ inline unsigned nblk(long n, int t = 256) { return (unsigned)std::max<long>(1, (
 
 // z_0 = chi_mu * B, z_L = 1; identity carry C0[(mu*B + k)][mu0][k0] = delta delta;
 // drive coefficient rewrite of the H1 block of core 0; reset per-step stats.
-__global__ void k_step_begin(int* d, int L, int B, zd* C0, long c0_cap, zd* W0, const zd* h1c0, int D1tot,
-                             int drive_off, int drive_D1, const double* f, long long n_f, const long long* step,
-                             double dt, double* stats) {
+__device__ void step_begin_body(const StepBeginArgs& a) {
+  int* d = a.d;
+  const int L = a.L, B = a.B;
   int mu = d[0];
   int zl = mu * B;
   long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  const long stride = (long)gridDim.x * blockDim.x;
   if (tid == 0) {
     d[L + 1] = zl;
     d[2 * L + 1] = 1;
-    stats[2] = 0.0;
+    a.stats[2] = 0.0;
   }
   long n = (long)zl * mu * B;
-  for (long x = tid; x < n && x < c0_cap; x += (long)gridDim.x * blockDim.x) {
+  for (long x = tid; x < n && x < a.c0_cap; x += stride) {
     long lp = x / ((long)mu * B);
     long rem = x % ((long)mu * B);
     long mu0 = rem / B, k0 = rem % B;
     long muv = lp / B, kv = lp % B;
-    C0[x] = mk<double>((muv == mu0 && kv == k0) ? 1.0 : 0.0, 0.0);
+    a.C0[x] = mk<double>((muv == mu0 && kv == k0) ? 1.0 : 0.0, 0.0);
   }
-  if (W0 && h1c0) {
-    long long sidx = *step;
-    double fv = (sidx < n_f) ? f[sidx] : 0.0;
-    zd c = mk<double>(0.0, -dt * fv);  // -i dt f(t_n)
+  if (a.W0 && a.h1c0) {
+    long long sidx = *a.step;
+    double fv = (sidx < a.n_f) ? a.f[sidx] : 0.0;
+    zd c = mk<double>(0.0, -a.dt * fv);  // -i dt f(t_n)
     // step layout [s'][a][s][b] with a = branch 0; H1 core 0 in builder layout [1][(2s'+s)][j]
-    long ne = 4L * drive_D1;
-    for (long x = tid; x < ne; x += (long)gridDim.x * blockDim.x) {
-      int p = (int)(x / drive_D1), j = (int)(x % drive_D1);
+    long ne = 4L * a.drive_D1;
+    for (long x = tid; x < ne; x += stride) {
+      int p = (int)(x / a.drive_D1), j = (int)(x % a.drive_D1);
       int so = p >> 1, si = p & 1;
-      W0[(((long)so * B + 0) * 2 + si) * D1tot + drive_off + j] = cmul(c, h1c0[x]);
+      a.W0[(((long)so * B + 0) * 2 + si) * a.D1tot + a.drive_off + j] = cmul(c, a.h1c0[x]);
     }
   }
 }
+__global__ void k_step_begin(StepBeginArgs a) { step_begin_body(a); }
+__global__ void k_step_begin_grp(const StepBeginArgs* __restrict__ a) { step_begin_body(a[blockIdx.y]); }
 
-__global__ void k_step_end(long long* step, int count) {
-  if (count && threadIdx.x == 0 && blockIdx.x == 0) (*step)++;
+__global__ void k_step_end(StepEndArgs a) {
+  if (a.count && threadIdx.x == 0 && blockIdx.x == 0) (*a.step)++;
+}
+__global__ void k_step_end_grp(const StepEndArgs* __restrict__ a) {
+  const StepEndArgs x = a[blockIdx.y];
+  if (x.count && threadIdx.x == 0 && blockIdx.x == 0) (*x.step)++;
 }
 
 // z_i = d_i for every bond (truncate-only pass has no zip-up)
@@ -76,10 +83,13 @@ __global__ void k_zip_from_state(int* d, int L) {
 }
 
 // dst[x] = src[x] for x < c * d[a] * d[b]
-__global__ void k_copy(zd* dst, const zd* src, DimExpr cnt, const int* d) {
-  long n = dev_eval(cnt, d);
-  for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < n; x += (long)gridDim.x * blockDim.x) dst[x] = src[x];
+__device__ void copy_body(const CopyArgs& c) {
+  long n = dev_eval(c.cnt, c.d);
+  for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < n; x += (long)gridDim.x * blockDim.x)
+    c.dst[x] = c.src[x];
 }
+__global__ void k_copy(CopyArgs c) { copy_body(c); }
+__global__ void k_copy_grp(const CopyArgs* __restrict__ c) { copy_body(c[blockIdx.y]); }
 
 __global__ void k_sum_abs2(const zd* p, DimExpr cnt, const int* d, double* out) {
   __shared__ double sh[32];
@@ -211,13 +221,26 @@ static inline void debug_dump(qlb_state*, int, const void*) {}
 
 static qlb_status gemm(qlb_state* st, GemmDesc& g) {
   qlb_ctx* ctx = st->sys->ctx;
-  cudaEvent_t a;
-  prof_before(ctx, st->stream, g.kclass, &a);
-  double* pf = ctx->prof_on ? ctx->d_prof + g.kclass : nullptr;
   if (!g.ws && st->Wsk && st->nWsk >= gemm_workspace_elems(gemm_grid_default())) g.ws = st->Wsk;
   // the mixed forms multiply in double-float (FP64 operands and results)
   if (st->prec != QLB_PREC_F64)
     g.df64 = ctx->opt.mixed_gemm >= 2 || (ctx->opt.mixed_gemm == 1 && g.kclass != QLB_K_GRAM);
+  if (st->rec) {
+    LaunchRec r;
+    r.kind = (st->prec == QLB_PREC_TC && g.kclass == QLB_K_CONTRACT) ? REC_GEMM_TC : REC_GEMM;
+    r.kclass = g.kclass;
+    r.df = g.df64;
+    r.g = g;
+    r.g.dims = st->d_dims;
+    r.g.split_grid = gemm_grid_default();
+    r.err = st->d_err;
+    r.dims = st->d_dims;
+    st->rec->push_back(r);
+    return QLB_OK;
+  }
+  cudaEvent_t a;
+  prof_before(ctx, st->stream, g.kclass, &a);
+  double* pf = ctx->prof_on ? ctx->d_prof + g.kclass : nullptr;
   // the tensor-core form runs the MPO application (the zip-up contractions) in
   // 3xTF32 on tcgen05; everything feeding a truncation decision stays FP64
   cudaError_t e = (st->prec == QLB_PREC_TC && g.kclass == QLB_K_CONTRACT)
@@ -234,10 +257,21 @@ static qlb_status gemm(qlb_state* st, GemmDesc& g) {
 
 static qlb_status eig(qlb_state* st, EigDesc& e) {
   qlb_ctx* ctx = st->sys->ctx;
+  e.solver_stats = ctx->d_solver;
+  if (st->rec) {
+    LaunchRec r;
+    r.kind = REC_EIG;
+    r.kclass = QLB_K_EIG;
+    r.df = st->prec != QLB_PREC_F64;
+    r.e = e;
+    r.e.dims = st->d_dims;
+    r.e.work = st->eigw;
+    st->rec->push_back(r);
+    return QLB_OK;
+  }
   cudaEvent_t a;
   prof_before(ctx, st->stream, QLB_K_EIG, &a);
   double* pf = ctx->prof_on ? ctx->d_prof + QLB_K_EIG : nullptr;
-  e.solver_stats = ctx->d_solver;
   // the mixed form runs the same Jacobi in double-float on the FP32 pipes
   cudaError_t r = st->prec != QLB_PREC_F64 ? launch_eig<df64>(e, st->d_dims, st->stream, st->eigw, pf)
                                            : launch_eig<double>(e, st->d_dims, st->stream, st->eigw, pf);
@@ -256,11 +290,22 @@ static qlb_status eig(qlb_state* st, EigDesc& e) {
 static qlb_status zip_range(qlb_state* st, EigDesc& e) {
   qlb_ctx* ctx = st->sys->ctx;
   if (!ctx->opt.zip_solver) return eig(st, e);
+  e.solver_stats = ctx->d_solver;
+  e.gate = st->d_gate;
+  if (st->rec) {
+    LaunchRec r;
+    r.kind = REC_ZIPQR;
+    r.kclass = QLB_K_EIG;
+    r.df = st->prec != QLB_PREC_F64;
+    r.e = e;
+    r.e.dims = st->d_dims;
+    r.e.work = st->eigw;
+    st->rec->push_back(r);
+    return eig(st, e);
+  }
   cudaEvent_t a;
   prof_before(ctx, st->stream, QLB_K_EIG, &a);
   double* pf = ctx->prof_on ? ctx->d_prof + QLB_K_EIG : nullptr;
-  e.solver_stats = ctx->d_solver;
-  e.gate = st->d_gate;
   cudaError_t r = st->prec != QLB_PREC_F64 ? launch_zipqr<df64>(e, st->d_dims, st->stream, st->eigw, pf)
                                            : launch_zipqr<double>(e, st->d_dims, st->stream, st->eigw, pf);
   prof_after(ctx, st->stream, QLB_K_EIG, a);
@@ -274,9 +319,19 @@ static qlb_status zip_range(qlb_state* st, EigDesc& e) {
 
 static qlb_status copy(qlb_state* st, zd* dst, const zd* src, DimExpr cnt, long max_n) {
   qlb_ctx* ctx = st->sys->ctx;
+  const CopyArgs c{dst, src, cnt, st->d_dims};
+  if (st->rec) {
+    LaunchRec r;
+    r.kind = REC_COPY;
+    r.kclass = QLB_K_OTHER;
+    r.c = c;
+    r.grid_n = max_n;
+    st->rec->push_back(r);
+    return QLB_OK;
+  }
   cudaEvent_t a;
   prof_before(ctx, st->stream, QLB_K_OTHER, &a);
-  k_copy<<<nblk(max_n), 256, 0, st->stream>>>(dst, src, cnt, st->d_dims);
+  k_copy<<<nblk(max_n), 256, 0, st->stream>>>(c);
   prof_after(ctx, st->stream, QLB_K_OTHER, a);
   QLB_CUDA_TRY(cudaGetLastError());
   return QLB_OK;
@@ -863,14 +918,25 @@ qlb_status enqueue_step(qlb_state* st, const Kraus& K, bool count_step) {
   auto cap = [&](int idx) { return hd[idx]; };
   qlb_status s;
   {
-    cudaEvent_t a;
-    prof_before(ctx, st->stream, QLB_K_OTHER, &a);
     long n0 = (long)cap(ZB(st, 0)) * cap(SB(0)) * K.B;
-    k_step_begin<<<nblk(n0), 256, 0, st->stream>>>(
-        st->d_dims, L, K.B, st->Cin, (long)st->nC, K.driven ? K.W[0] : nullptr, K.driven ? K.drive_core0 : nullptr,
-        K.D[1], K.drive_off, K.drive_D1, st->sys->d_f, st->sys->n_f, st->d_step, K.dt, st->d_stats);
-    prof_after(ctx, st->stream, QLB_K_OTHER, a);
-    QLB_CUDA_TRY(cudaGetLastError());
+    const StepBeginArgs ba{st->d_dims,   L,         K.B,         st->Cin,         (long)st->nC,
+                           K.driven ? K.W[0] : nullptr,          K.driven ? K.drive_core0 : nullptr,
+                           K.D[1],       K.drive_off, K.drive_D1, st->sys->d_f,    st->sys->n_f,
+                           st->d_step,   K.dt,      st->d_stats};
+    if (st->rec) {
+      LaunchRec r;
+      r.kind = REC_BEGIN;
+      r.kclass = QLB_K_OTHER;
+      r.b = ba;
+      r.grid_n = std::max<long>(n0, 4L * K.drive_D1);
+      st->rec->push_back(r);
+    } else {
+      cudaEvent_t a;
+      prof_before(ctx, st->stream, QLB_K_OTHER, &a);
+      k_step_begin<<<nblk(n0), 256, 0, st->stream>>>(ba);
+      prof_after(ctx, st->stream, QLB_K_OTHER, a);
+      QLB_CUDA_TRY(cudaGetLastError());
+    }
   }
   zd* Cin = st->Cin;
   zd* Cout = st->Cout;
@@ -969,11 +1035,20 @@ qlb_status enqueue_step(qlb_state* st, const Kraus& K, bool count_step) {
   }
   if ((s = enqueue_compress(st, hd))) return s;
   {
-    cudaEvent_t a;
-    prof_before(ctx, st->stream, QLB_K_OTHER, &a);
-    k_step_end<<<1, 32, 0, st->stream>>>(st->d_step, count_step ? 1 : 0);
-    prof_after(ctx, st->stream, QLB_K_OTHER, a);
-    QLB_CUDA_TRY(cudaGetLastError());
+    const StepEndArgs ea{st->d_step, count_step ? 1 : 0};
+    if (st->rec) {
+      LaunchRec r;
+      r.kind = REC_END;
+      r.kclass = QLB_K_OTHER;
+      r.x = ea;
+      st->rec->push_back(r);
+    } else {
+      cudaEvent_t a;
+      prof_before(ctx, st->stream, QLB_K_OTHER, &a);
+      k_step_end<<<1, 32, 0, st->stream>>>(ea);
+      prof_after(ctx, st->stream, QLB_K_OTHER, a);
+      QLB_CUDA_TRY(cudaGetLastError());
+    }
   }
   return QLB_OK;
 }
@@ -1016,6 +1091,11 @@ qlb_status run_steps(qlb_state* st, int64_t n, bool sync) {
   st->host_steps += n;
   if (!sync) return QLB_OK;
   QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
+  return check_flags(st);
+}
+
+// The state's device error flags and trace after its work has completed.
+qlb_status check_flags(qlb_state* st) {
   int err = 0;
   QLB_CUDA_TRY(cudaMemcpy(&err, st->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (err) {
@@ -1201,6 +1281,190 @@ qlb_status kraus_branch(qlb_state* st, int k, Mpo& out) {
   }
   QLB_CUDA_TRY(cudaGetLastError());
   QLB_CUDA_TRY(cudaStreamSynchronize(st->stream));
+  return QLB_OK;
+}
+
+// ------------------------------------------------------------------ groups
+//
+// A group steps S states with one launch per position of the step: each member's
+// step is recorded (the same helpers, with every pointer and shape of that
+// member), the records are checked to form the same launch sequence, the members'
+// descriptors go to one device table, and the grouped launches (blockIdx.y =
+// member) are captured once as a CUDA graph on the group's stream.  A member's
+// launch computes exactly what its own launch computes: the same kernels, the same
+// K split of its GEMMs (decided on the full grid) and the same reduction orders.
+
+void GroupExec::release() {
+  if (graph) cudaGraphExecDestroy(graph);
+  graph = nullptr;
+  if (d_tab) dev_free(ctx, d_tab);
+  d_tab = nullptr;
+  keys.clear();
+  who.clear();
+  launches = 0;
+}
+
+static size_t rec_row_bytes(int kind) {
+  switch (kind) {
+    case REC_GEMM:
+      return sizeof(GemmDesc);
+    case REC_ZIPQR:
+    case REC_EIG:
+      return sizeof(EigDesc);
+    case REC_COPY:
+      return sizeof(CopyArgs);
+    case REC_BEGIN:
+      return sizeof(StepBeginArgs);
+    case REC_END:
+      return sizeof(StepEndArgs);
+    default:
+      return 0;  // REC_GEMM_TC: launched member by member
+  }
+}
+
+static qlb_status group_capture(GroupExec& gx, const std::vector<qlb_state*>& ms, cudaStream_t gs) {
+  qlb_ctx* ctx = gx.ctx;
+  const int S = (int)ms.size();
+  // the previous graph may still run and read the table that is replaced below
+  QLB_CUDA_TRY(cudaStreamSynchronize(gs));
+  std::vector<std::vector<LaunchRec>> recs(S);
+  for (int m = 0; m < S; m++) {
+    ms[m]->rec = &recs[m];
+    qlb_status s = enqueue_step(ms[m], ms[m]->kraus, true);
+    ms[m]->rec = nullptr;
+    if (s) return s;
+  }
+  const size_t P = recs[0].size();
+  for (int m = 1; m < S; m++) {
+    bool same = recs[m].size() == P;
+    for (size_t p = 0; same && p < P; p++)
+      same = recs[m][p].kind == recs[0][p].kind && recs[m][p].df == recs[0][p].df;
+    if (!same) {
+      set_error("the states of a group must step the same launch sequence (same sites, precision form and scheme)");
+      return QLB_EINVAL;
+    }
+  }
+  for (size_t p = 0; p < P; p++)
+    if (recs[0][p].kind == REC_GEMM)
+      for (int m = 0; m < S; m++)
+        if (!recs[m][p].g.ws) {
+          set_error("group GEMM without a workspace");
+          return QLB_EINVAL;
+        }
+  // the table: for each position, S rows of its argument type, 16-byte aligned
+  std::vector<size_t> off(P, 0);
+  size_t total = 0;
+  for (size_t p = 0; p < P; p++) {
+    off[p] = total;
+    total += ((size_t)S * rec_row_bytes(recs[0][p].kind) + 15) & ~(size_t)15;
+  }
+  std::vector<unsigned char> host(std::max<size_t>(total, 16));
+  for (size_t p = 0; p < P; p++) {
+    const size_t rb = rec_row_bytes(recs[0][p].kind);
+    for (int m = 0; m < S && rb; m++) {
+      const LaunchRec& r = recs[m][p];
+      const void* src = nullptr;
+      switch (r.kind) {
+        case REC_GEMM: src = &r.g; break;
+        case REC_ZIPQR:
+        case REC_EIG: src = &r.e; break;
+        case REC_COPY: src = &r.c; break;
+        case REC_BEGIN: src = &r.b; break;
+        case REC_END: src = &r.x; break;
+      }
+      std::memcpy(host.data() + off[p] + (size_t)m * rb, src, rb);
+    }
+  }
+  gx.release();
+  qlb_status s;
+  if ((s = dev_alloc(ctx, &gx.d_tab, host.size()))) return s;
+  QLB_CUDA_TRY(cudaMemcpyAsync(gx.d_tab, host.data(), host.size(), cudaMemcpyHostToDevice, gs));
+  QLB_CUDA_TRY(cudaStreamSynchronize(gs));
+  unsigned char* tab = (unsigned char*)gx.d_tab;
+  QLB_CUDA_TRY(cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  int launches = 0;
+  for (size_t p = 0; p < P && e == cudaSuccess; p++) {
+    const LaunchRec& r0 = recs[0][p];
+    unsigned char* t = tab + off[p];
+    long maxn = 1;
+    int n_max = 1;
+    for (int m = 0; m < S; m++) {
+      maxn = std::max(maxn, recs[m][p].grid_n);
+      n_max = std::max(n_max, recs[m][p].e.n_max);
+    }
+    launches++;
+    switch (r0.kind) {
+      case REC_BEGIN:
+        k_step_begin_grp<<<dim3(nblk(maxn), S), 256, 0, gs>>>((const StepBeginArgs*)t);
+        e = cudaGetLastError();
+        break;
+      case REC_END:
+        k_step_end_grp<<<dim3(1, S), 32, 0, gs>>>((const StepEndArgs*)t);
+        e = cudaGetLastError();
+        break;
+      case REC_COPY:
+        k_copy_grp<<<dim3(nblk(maxn), S), 256, 0, gs>>>((const CopyArgs*)t);
+        e = cudaGetLastError();
+        break;
+      case REC_GEMM:
+        e = launch_gemm_group((const GemmDesc*)t, S, r0.df, gs, nullptr);
+        break;
+      case REC_GEMM_TC:
+        launches += S - 1;
+        for (int m = 0; m < S && e == cudaSuccess; m++)
+          e = launch_gemm_tc(recs[m][p].g, recs[m][p].dims, gs, recs[m][p].err, nullptr);
+        break;
+      case REC_ZIPQR:
+        e = r0.df ? launch_zipqr_group<df64>(n_max, (const EigDesc*)t, S, gs, nullptr)
+                  : launch_zipqr_group<double>(n_max, (const EigDesc*)t, S, gs, nullptr);
+        break;
+      case REC_EIG:
+        e = r0.df ? launch_eig_group<df64>(n_max, (const EigDesc*)t, S, gs, nullptr)
+                  : launch_eig_group<double>(n_max, (const EigDesc*)t, S, gs, nullptr);
+        break;
+    }
+  }
+  cudaGraph_t gr = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(gs, &gr);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    set_error(std::string("group capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return QLB_EDEVICE;
+  }
+  e = cudaGraphInstantiate(&gx.graph, gr, 0);
+  cudaGraphDestroy(gr);
+  QLB_CUDA_TRY(e);
+  gx.keys.resize(S);
+  gx.who.assign(ms.begin(), ms.end());
+  for (int m = 0; m < S; m++) gx.keys[m] = ms[m]->plan_key;
+  gx.launches = launches;
+  return QLB_OK;
+}
+
+qlb_status group_run(GroupExec& gx, const std::vector<qlb_state*>& ms, cudaStream_t gs, cudaEvent_t ev, int64_t n,
+                     bool sync) {
+  if (n <= 0 || ms.empty()) return QLB_OK;
+  bool fresh = gx.graph && gx.keys.size() == ms.size() && gx.who.size() == ms.size();
+  for (size_t m = 0; fresh && m < ms.size(); m++) fresh = gx.who[m] == ms[m] && gx.keys[m] == ms[m]->plan_key;
+  qlb_status s;
+  // the members' earlier work (their own streams) comes first
+  for (qlb_state* st : ms) {
+    QLB_CUDA_TRY(cudaEventRecord(ev, st->stream));
+    QLB_CUDA_TRY(cudaStreamWaitEvent(gs, ev, 0));
+  }
+  if (!fresh && (s = group_capture(gx, ms, gs))) return s;
+  for (int64_t k = 0; k < n; k++) QLB_CUDA_TRY(cudaGraphLaunch(gx.graph, gs));
+  // and their later work waits for the group's steps
+  QLB_CUDA_TRY(cudaEventRecord(ev, gs));
+  for (qlb_state* st : ms) {
+    QLB_CUDA_TRY(cudaStreamWaitEvent(st->stream, ev, 0));
+    st->host_steps += n;
+  }
+  if (!sync) return QLB_OK;
+  QLB_CUDA_TRY(cudaStreamSynchronize(gs));
+  for (qlb_state* st : ms)
+    if ((s = check_flags(st))) return s;
   return QLB_OK;
 }
 

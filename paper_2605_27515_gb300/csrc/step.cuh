@@ -22,6 +22,24 @@ qlb_status truncate_pass(qlb_state* st);
 qlb_status state_sum_abs2_site0(qlb_state* st, double* out);
 // Runs n steps (CUDA graph unless profiling) and checks the device error flags.
 qlb_status run_steps(qlb_state* st, int64_t n, bool sync);
+// The state's device error flags and trace, read after its work has completed.
+qlb_status check_flags(qlb_state* st);
+
+// The captured step of a group of states (one launch per position over all members).
+struct GroupExec {
+  qlb_ctx* ctx = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<int> keys;   // members' plan keys at capture
+  std::vector<const qlb_state*> who;  // the members at capture
+  void* d_tab = nullptr;   // device table of the members' launch descriptors
+  int launches = 0;        // kernel launches per captured step
+  void release();
+};
+// Steps the members n times on stream gs (ordered after, and before, the work of
+// their own streams through ev); re-records and re-captures when a member's plan
+// changed.  Each member's Kraus MPO and buffers must be planned for the step.
+qlb_status group_run(GroupExec& gx, const std::vector<qlb_state*>& ms, cudaStream_t gs, cudaEvent_t ev, int64_t n,
+                     bool sync);
 // Host copy of the state bonds.
 qlb_status read_dims(qlb_state* st, std::vector<int>& d);
 // Branch k of the current Kraus MPO as a builder-layout MPO (left boundary 1).

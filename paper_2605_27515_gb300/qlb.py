@@ -117,6 +117,11 @@ _SIGS = {
     "qlb_profile_read": (_st, [_vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                C.POINTER(C.c_double)]),
     "qlb_profile_reset": (_st, [_vp]),
+    "qlb_group_create": (_st, [_vp, C.POINTER(_vp), C.c_int, C.POINTER(_vp)]),
+    "qlb_group_destroy": (None, [_vp]),
+    "qlb_group_step": (_st, [_vp, C.c_double, C.c_int64]),
+    "qlb_group_launches": (_st, [_vp, C.POINTER(C.c_int)]),
+    "qlb_group_stream": (_st, [_vp, C.POINTER(_vp)]),
 }
 
 
@@ -483,6 +488,43 @@ def qlb_eig_check(device: int, precision: int, solver: int, G, tol: float = 0.0,
                                 C.byref(ms)))
     kk = k.value
     return lam, (V[:n * kk].reshape(n, kk) if kk > 0 else None), kk, ms.value
+
+
+class Group:
+    """States stepped together, one launch per phase of the step over all of them
+    (qlb_group_*).  Close the group before its states."""
+
+    def __init__(self, ctx: Ctx, states):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.states = list(states)
+        arr = (_vp * len(self.states))(*[st.h for st in self.states])
+        h = _vp()
+        _check(self.lib.qlb_group_create(ctx.h, arr, len(self.states), C.byref(h)))
+        self.h = h
+
+    def step(self, dt, n=1) -> int:
+        return _check(self.lib.qlb_group_step(self.h, float(dt), int(n)))
+
+    def launches(self) -> int:
+        v = C.c_int()
+        _check(self.lib.qlb_group_launches(self.h, C.byref(v)))
+        return v.value
+
+    def stream(self) -> int:
+        s = _vp()
+        _check(self.lib.qlb_group_stream(self.h, C.byref(s)))
+        return s.value or 0
+
+    def close(self):
+        if self.h:
+            self.lib.qlb_group_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
