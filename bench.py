@@ -415,14 +415,21 @@ def run_other_workload(args):
         ctx.load_tuning(tuning)
     dt = cfg["dt"]
     n_total = args.warmup + args.steps + 1
+    t_start = time.perf_counter()
+
+    def progress(what):
+        print(f"[bench {args.workload}] {time.perf_counter() - t_start:7.1f} s  {what}", file=sys.stderr, flush=True)
+
     if args.workload == "transmon":
         builds = [systems.build(ctx, cfg, nsteps=n_total)]
     else:
         builds = [systems.build(ctx, cfg, J=J) for J in inputs.cat_pair_J(cfg["n_variants"], cfg["J"])]
+    progress(f"{len(builds)} systems built")
     states = [b.sys.state(b.init) for b in builds]
     for st in states:
         st.step(dt, args.warmup)
     ctx.synchronize()
+    progress("warm-up steps done")
     snaps = [st.export() for st in states]
     ctx.profile_reset()
     torch.cuda.synchronize()
@@ -434,6 +441,7 @@ def run_other_workload(args):
     ctx.synchronize()
     wall_streams = time.perf_counter() - t0
     per_stream_end = [st.bond_dims() for st in states]
+    progress("per-stream window done")
     # the same steps again from the same snapshots as one group (one launch per
     # phase of the step over all states)
     for st, sn in zip(states, snaps):
@@ -442,6 +450,7 @@ def run_other_workload(args):
     if grp is not None:
         grp.step(dt, 1)  # records and captures the group's graph
         ctx.synchronize()
+        progress(f"group captured ({grp.launches()} launches per step)")
         for st, sn in zip(states, snaps):
             st.import_(sn)
         ctx.synchronize()
@@ -457,6 +466,7 @@ def run_other_workload(args):
                 states[0].step(dt, 1)
         ctx.synchronize()
         wall = time.perf_counter() - t0
+    progress("timed window done")
     same_as_streams = [st.bond_dims() for st in states] == per_stream_end
     launches = grp.launches() if grp is not None else None
     if grp is not None:

@@ -48,6 +48,7 @@ size_t tc_gemm_smem_bytes();
 cudaError_t launch_gemm_group(const GemmDesc* d_grp, int S, int use_df, cudaStream_t s, double* prof);
 template <typename R>
 cudaError_t launch_eig_group(int n_max, const EigDesc* d_grp, int S, cudaStream_t s, double* prof);
+size_t eig_group_workspace_elems(int n_max, int group_n_max);
 template <typename R>
 cudaError_t launch_zipqr_group(int n_max, const EigDesc* d_grp, int S, cudaStream_t s, double* prof);
 void init_tc_attributes();

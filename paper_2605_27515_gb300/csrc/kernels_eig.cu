@@ -965,6 +965,19 @@ size_t eig_workspace_elems(int n_max) {
   return need * sizeof(zd) > limit ? need : 1;
 }
 
+// Workspace a member of planned size n_max needs when a grouped launch serves it
+// with the kernel picked for the group's largest planned size group_n_max: the
+// one-CTA kernel (group_n_max <= 24 or above the cluster range) sizes its shared
+// memory for group_n_max, capped, and falls back to the member's workspace for
+// problems that do not fit; the cluster kernels need none.
+size_t eig_group_workspace_elems(int n_max, int group_n_max) {
+  if (group_n_max > 24 && group_n_max <= EIG_CL_MAX_NP) return 1;
+  const size_t dyn = std::min(eig_smem_bytes<double>(group_n_max), (size_t)EIG_SMEM_LIMIT);
+  const int np = n_max + (n_max & 1);
+  const size_t need = 2 * (size_t)np * np;
+  return need * sizeof(zd) > dyn ? need : 1;
+}
+
 template <typename R, int C>
 cudaError_t launch_eig_cl(const EigDesc& e, const int* d_dims, cudaStream_t s, double* prof,
                           const EigDesc* grp = nullptr, int S = 1) {

@@ -80,14 +80,18 @@ __device__ __forceinline__ cx<R> gemm_alpha(const GemmDesc& g) {
 // R: the storage type of A, B, C; Cm: the type the products are formed and summed in
 // (R itself, or double-float for FP64 storage in the mixed forms)
 template <typename R, typename Cm, bool GRP>
-__global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc g, const int* __restrict__ d, double* prof,
+__global__ void __launch_bounds__(G_THREADS) k_gemm(const GemmDesc g_in, const int* __restrict__ d_in, double* prof,
                                                     const GemmDesc* __restrict__ grp) {
   // grouped launch: this CTA works on member blockIdx.y, whose descriptor (and dims)
-  // come from the group's table; the K split is decided on the member's nominal grid
+  // come from the group's table (kept in shared memory, not registers); the K split
+  // is decided on the member's nominal grid
+  __shared__ GemmDesc s_g;
   if constexpr (GRP) {
-    g = grp[blockIdx.y];
-    d = g.dims;
+    if (threadIdx.x == 0) s_g = grp[blockIdx.y];
+    __syncthreads();
   }
+  const GemmDesc& g = GRP ? s_g : g_in;
+  const int* __restrict__ d = GRP ? s_g.dims : d_in;
   const int gnom = g.split_grid > 0 ? g.split_grid : (int)gridDim.x;
   const int m = dev_eval(g.m, d), n = dev_eval(g.n, d), K = dev_eval(g.k, d);
   const int nb1 = dev_eval(g.nb1, d), nb2 = dev_eval(g.nb2, d);
@@ -131,6 +135,10 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc g, const int* __res
     cx<R>* C = (cx<R>*)g.C + (long)b1 * dev_eval(g.sC1, d) + (long)b2 * dev_eval(g.sC2, d);
     const int kbeg = kp * chunk, kend = min(K, kbeg + chunk);
 
+    // warp-uniform: does this warp own an output row of the tile (rows 2w, 2w + 1
+    // of each half), and does the tile reach the upper column half
+    const int wrow = row0 + 2 * (tid >> 5);
+    const bool do_r0 = wrow < m, do_r1 = wrow + 16 < m, do_c1 = col0 + 16 < n;
     cx<Cm> acc[2][2];
 #pragma unroll
     for (int i = 0; i < 2; i++)
@@ -173,24 +181,45 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc g, const int* __res
         Bs[kk][j] = to_c<Cm>(v);
       }
       __syncthreads();
+      // the products of the padding are skipped where a whole warp would form only
+      // padding (warp-uniform tests: the warp's rows, the upper column half, the
+      // K tail), which on the slow FP64 pipe is most of the work of a small GEMM
+      const int kn = min(GB_K, kend - k0);
+      if (kn == GB_K && do_r1 && do_c1) {
 #pragma unroll
-      for (int kk = 0; kk < GB_K; kk++) {
-        cx<Cm> a0 = As[kk][ty], a1 = As[kk][ty + 16];
-        cx<Cm> b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
-        cmac(acc[0][0], a0, b0);
-        cmac(acc[0][1], a0, b1);
-        cmac(acc[1][0], a1, b0);
-        cmac(acc[1][1], a1, b1);
+        for (int kk = 0; kk < GB_K; kk++) {
+          cx<Cm> a0 = As[kk][ty], a1 = As[kk][ty + 16];
+          cx<Cm> b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+          cmac(acc[0][0], a0, b0);
+          cmac(acc[0][1], a0, b1);
+          cmac(acc[1][0], a1, b0);
+          cmac(acc[1][1], a1, b1);
+        }
+      } else if (do_r0) {
+#pragma unroll 4
+        for (int kk = 0; kk < kn; kk++) {
+          cx<Cm> a0 = As[kk][ty];
+          cx<Cm> b0 = Bs[kk][tx];
+          cmac(acc[0][0], a0, b0);
+          if (do_c1) cmac(acc[0][1], a0, Bs[kk][tx + 16]);
+          if (do_r1) {
+            cx<Cm> a1 = As[kk][ty + 16];
+            cmac(acc[1][0], a1, b0);
+            if (do_c1) cmac(acc[1][1], a1, Bs[kk][tx + 16]);
+          }
+        }
       }
       __syncthreads();
     }
     if (ks > 1) {
       // partial tile of this K part; the last CTA of the tile adds them in order
       cx<Cm>* P = part_ws + ((long)kp * ntiles + tile) * GB_TILE;
+      // (only the entries inside the output are written and read back)
 #pragma unroll
       for (int i = 0; i < 2; i++)
 #pragma unroll
-        for (int j = 0; j < 2; j++) P[(ty + 16 * i) * GB_N + tx + 16 * j] = acc[i][j];
+        for (int j = 0; j < 2; j++)
+          if (row0 + ty + 16 * i < m && col0 + tx + 16 * j < n) P[(ty + 16 * i) * GB_N + tx + 16 * j] = acc[i][j];
       __threadfence();
       __syncthreads();
       if (tid == 0) s_last = atomicAdd(counters + tile, 1) == ks - 1;
@@ -201,12 +230,19 @@ __global__ void __launch_bounds__(G_THREADS) k_gemm(GemmDesc g, const int* __res
       for (int i = 0; i < 2; i++)
 #pragma unroll
         for (int j = 0; j < 2; j++) {
+          if (row0 + ty + 16 * i >= m || col0 + tx + 16 * j >= n) continue;
           cx<Cm> sum = to_c<Cm>(mk<R>(0, 0));
           const long off = (long)(ty + 16 * i) * GB_N + tx + 16 * j;
-          for (int s = 0; s < ks; s++) {
-            const cx<Cm>* Ps = part_ws + ((long)s * ntiles + tile) * GB_TILE + off;
-            sum = cadd(sum, ldcg_cx(Ps));
+          const long pstride = ntiles * GB_TILE;
+          const cx<Cm>* P0 = part_ws + tile * GB_TILE + off;
+          int s = 0;
+          // four independent loads in flight, added in part order
+          for (; s + 4 <= ks; s += 4) {
+            const cx<Cm> v0 = ldcg_cx(P0 + s * pstride), v1 = ldcg_cx(P0 + (s + 1) * pstride);
+            const cx<Cm> v2 = ldcg_cx(P0 + (s + 2) * pstride), v3 = ldcg_cx(P0 + (s + 3) * pstride);
+            sum = cadd(cadd(cadd(cadd(sum, v0), v1), v2), v3);
           }
+          for (; s < ks; s++) sum = cadd(sum, ldcg_cx(P0 + s * pstride));
           acc[i][j] = sum;
         }
       if (tid == 0) counters[tile] = 0;  // ready for the next launch on this workspace

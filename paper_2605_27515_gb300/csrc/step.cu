@@ -1328,11 +1328,36 @@ static qlb_status group_capture(GroupExec& gx, const std::vector<qlb_state*>& ms
   // the previous graph may still run and read the table that is replaced below
   QLB_CUDA_TRY(cudaStreamSynchronize(gs));
   std::vector<std::vector<LaunchRec>> recs(S);
-  for (int m = 0; m < S; m++) {
-    ms[m]->rec = &recs[m];
-    qlb_status s = enqueue_step(ms[m], ms[m]->kraus, true);
-    ms[m]->rec = nullptr;
-    if (s) return s;
+  for (int pass = 0; pass < 2; pass++) {
+    for (int m = 0; m < S; m++) {
+      recs[m].clear();
+      ms[m]->rec = &recs[m];
+      qlb_status s = enqueue_step(ms[m], ms[m]->kraus, true);
+      ms[m]->rec = nullptr;
+      if (s) return s;
+    }
+    if (pass == 1) break;
+    // an eigen-solve served by the kernel of a larger co-member may need more
+    // workspace than the member's own plan gave it: grow it, then record again
+    // (the records hold the workspace pointers)
+    bool grown = false;
+    for (size_t p = 0; p < recs[0].size(); p++) {
+      if (recs[0][p].kind != REC_EIG) continue;
+      int gmax = 1;
+      for (int m = 0; m < S; m++)
+        if (p < recs[m].size()) gmax = std::max(gmax, recs[m][p].e.n_max);
+      for (int m = 0; m < S; m++) {
+        if (p >= recs[m].size()) continue;
+        const size_t need = eig_group_workspace_elems(recs[m][p].e.n_max, gmax);
+        if (need > ms[m]->nEw) {
+          qlb_status s = realloc_buf(ctx, &ms[m]->eigw, &ms[m]->nEw, need);
+          if (s) return s;
+          ms[m]->plan_key++;  // the member's own captured step used the old workspace
+          grown = true;
+        }
+      }
+    }
+    if (!grown) break;
   }
   const size_t P = recs[0].size();
   for (int m = 1; m < S; m++) {

@@ -68,7 +68,8 @@ def test_mixed_group_matches_alone_and_oracle():
     and different single-photon loss, one with a lower bond cap; 300 group steps
     agree with each twin alone within 1e-12 and with the dense oracle within 1e-6."""
     variants = [dict(alpha2=2.0, k1=1e-3), dict(alpha2=4.0, k1=3e-3), dict(alpha2=6.0, k1=1e-4)]
-    ctx = Q.Ctx(device=0, tol=1e-12, chi_max=16, chi_mu_max=8)
+    # purification cap 32 = N: only member 2's bond cap truncates
+    ctx = Q.Ctx(device=0, tol=1e-12, chi_max=16, chi_mu_max=32)
     builds = [systems.build(ctx, _cfg(**v)) for v in variants]
     members = [b.sys.state(b.init) for b in builds]
     twins = [b.sys.state(b.init) for b in builds]
@@ -90,6 +91,31 @@ def test_mixed_group_matches_alone_and_oracle():
             for name in ("n", "parity"):
                 o = D.expectation(rho, ds.observables[name]).real
                 assert abs(m.expectation(b.observables[name]).real - o) < 1e-6, (k, name)
+    g.close()
+    for st in members + twins:
+        st.close()
+    ctx.close()
+
+
+def test_group_of_multimode_variants_equals_alone():
+    """The four-mode cat pair at check size ([b1, a1, a2, b2] = [4, 8, 8, 4] levels,
+    five branches, 10 sites): four beam-splitter variants J as one group, 40 steps,
+    bit for bit against each variant stepped alone."""
+    cfg = inputs.config("cat_pair")
+    cfg["R"] = list(cfg["check"]["R"])
+    ctx = Q.Ctx(device=0, precision=Q.PREC_MIXED, tol=cfg["tol"], chi_max=32, chi_mu_max=16)
+    Js = inputs.cat_pair_J(4, cfg["J"] * 20)
+    builds = [systems.build(ctx, cfg, J=J) for J in Js]
+    members = [b.sys.state(b.init) for b in builds]
+    twins = [b.sys.state(b.init) for b in builds]
+    g = Q.Group(ctx, members)
+    g.step(cfg["dt"] * 20, 40)
+    for t in twins:
+        t.step(cfg["dt"] * 20, 40)
+    for b, m, t in zip(builds, members, twins):
+        assert m.bond_dims() == t.bond_dims()
+        for name in ("n_a1", "n_a2", "parity_a1"):
+            assert m.expectation(b.observables[name]) == t.expectation(b.observables[name]), name
     g.close()
     for st in members + twins:
         st.close()
