@@ -55,3 +55,22 @@ def test_no_device_gives_a_status(lib):
     h = C.c_void_p()
     assert lib.qlb_create(None, C.byref(h)) == Q.EDEVICE
     assert b"device" in lib.qlb_last_error()
+
+
+def test_group_calls_check_their_arguments(lib):
+    """The group calls return QLB_EINVAL for missing handles and impossible sizes
+    before touching a device."""
+    out = C.c_void_p()
+    arr = (C.c_void_p * 1)(None)
+    assert lib.qlb_group_create(None, arr, 1, C.byref(out)) == Q.EINVAL
+    fake_ctx = C.c_void_p(1)  # never dereferenced: the size check comes first
+    assert lib.qlb_group_create(fake_ctx, arr, 0, C.byref(out)) == Q.EINVAL
+    assert lib.qlb_group_create(fake_ctx, arr, 5000, C.byref(out)) == Q.EINVAL
+    assert lib.qlb_group_create(fake_ctx, arr, 1, C.byref(out)) == Q.EINVAL  # null state
+    assert not out.value
+    assert lib.qlb_group_step(None, 1e-3, 1) == Q.EINVAL
+    n = C.c_int()
+    assert lib.qlb_group_launches(None, C.byref(n)) == Q.EINVAL
+    s = C.c_void_p()
+    assert lib.qlb_group_stream(None, C.byref(s)) == Q.EINVAL
+    lib.qlb_group_destroy(None)  # a no-op
