@@ -35,6 +35,21 @@ namespace qlb {
 
 namespace {
 
+// The updates of a rotation, c x - s y and s x + c y (real c, complex s), written
+// as fused multiply-adds: FMAs in FP64, multiply-adds with one renormalisation in
+// double-float (about 40 % fewer FP32 instructions than separate products and
+// sums, at the same ~2^-44 relative accuracy).
+__device__ __forceinline__ double rmac(double c, double a, double b) { return fma(a, b, c); }
+__device__ __forceinline__ df64 rmac(df64 c, df64 a, df64 b) { return df_mac(c, a, b); }
+template <typename R>
+__device__ __forceinline__ cx<R> rot_cx_minus_sy(cx<R> x, R c, cx<R> s, cx<R> y) {
+  return mk<R>(rmac(rmac(c * x.re, -s.re, y.re), s.im, y.im), rmac(rmac(c * x.im, -s.re, y.im), -s.im, y.re));
+}
+template <typename R>
+__device__ __forceinline__ cx<R> rot_sx_plus_cy(cx<R> s, cx<R> x, R c, cx<R> y) {
+  return mk<R>(rmac(rmac(c * y.re, s.re, x.re), -s.im, x.im), rmac(rmac(c * y.im, s.re, x.im), s.im, x.re));
+}
+
 template <typename R>
 struct Eps;
 template <>
@@ -275,8 +290,8 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
         R c = rc[t];
         cx<R> sp = rsp[t];
         cx<R> gp = Gs[(long)p * np + j], gq = Gs[(long)q * np + j];
-        Gs[(long)p * np + j] = csub(cscale(gp, c), cmul(sp, gq));
-        Gs[(long)q * np + j] = cadd(cmul(cconj(sp), gp), cscale(gq, c));
+        Gs[(long)p * np + j] = rot_cx_minus_sy(gp, c, sp, gq);
+        Gs[(long)q * np + j] = rot_sx_plus_cy(cconj(sp), gp, c, gq);
       }
       __syncthreads();
       // columns: G <- G J, V <- V J; the pair's off-diagonal becomes an exact zero
@@ -288,8 +303,8 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
         R c = rc[t];
         cx<R> sp = rsp[t];
         cx<R> gp = Gs[(long)i * np + p], gq = Gs[(long)i * np + q];
-        cx<R> np_ = csub(cscale(gp, c), cmul(cconj(sp), gq));
-        cx<R> nq_ = cadd(cmul(sp, gp), cscale(gq, c));
+        cx<R> np_ = rot_cx_minus_sy(gp, c, cconj(sp), gq);
+        cx<R> nq_ = rot_sx_plus_cy(sp, gp, c, gq);
         if (i == p) {
           np_.im = zero;
           nq_ = mk<R>(zero, zero);
@@ -300,8 +315,8 @@ __global__ void __launch_bounds__(NT) k_eig(EigDesc e, int* __restrict__ d, cx<R
         Gs[(long)i * np + p] = np_;
         Gs[(long)i * np + q] = nq_;
         cx<R> vp = Vs[(long)i * np + p], vq = Vs[(long)i * np + q];
-        Vs[(long)i * np + p] = csub(cscale(vp, c), cmul(cconj(sp), vq));
-        Vs[(long)i * np + q] = cadd(cmul(sp, vp), cscale(vq, c));
+        Vs[(long)i * np + p] = rot_cx_minus_sy(vp, c, cconj(sp), vq);
+        Vs[(long)i * np + q] = rot_sx_plus_cy(sp, vp, c, vq);
       }
       __syncthreads();
     }
@@ -500,7 +515,7 @@ __global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, d
           const int partner = i == rr.p ? rr.q : rr.p;
           const int op = partner / rpb;
           const cx<R> gx = cluster.map_shared_rank(Gc, op)[(long)(partner - op * rpb) * np + j];
-          out = i == rr.p ? csub(cscale(gi, rr.c), cmul(rr.sp, gx)) : cadd(cmul(cconj(rr.sp), gx), cscale(gi, rr.c));
+          out = i == rr.p ? rot_cx_minus_sy(gi, rr.c, rr.sp, gx) : rot_sx_plus_cy(cconj(rr.sp), gx, rr.c, gi);
         }
         Gn[w] = out;
       }
@@ -512,8 +527,8 @@ __global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, d
         if (rr.p < 0) continue;
         const int p = rr.p, q = rr.q, i = r0 + li;
         cx<R> gp = Gn[(long)li * np + p], gq = Gn[(long)li * np + q];
-        cx<R> np_ = csub(cscale(gp, rr.c), cmul(cconj(rr.sp), gq));
-        cx<R> nq_ = cadd(cmul(rr.sp, gp), cscale(gq, rr.c));
+        cx<R> np_ = rot_cx_minus_sy(gp, rr.c, cconj(rr.sp), gq);
+        cx<R> nq_ = rot_sx_plus_cy(rr.sp, gp, rr.c, gq);
         if (i == p) {
           np_.im = zero;
           nq_ = mk<R>(zero, zero);
@@ -524,8 +539,8 @@ __global__ void __launch_bounds__(NT) k_eig_cl(EigDesc e, int* __restrict__ d, d
         Gn[(long)li * np + p] = np_;
         Gn[(long)li * np + q] = nq_;
         cx<R> vp = Vl[(long)li * np + p], vq = Vl[(long)li * np + q];
-        Vl[(long)li * np + p] = csub(cscale(vp, rr.c), cmul(cconj(rr.sp), vq));
-        Vl[(long)li * np + q] = cadd(cmul(rr.sp, vp), cscale(vq, rr.c));
+        Vl[(long)li * np + p] = rot_cx_minus_sy(vp, rr.c, cconj(rr.sp), vq);
+        Vl[(long)li * np + q] = rot_sx_plus_cy(rr.sp, vp, rr.c, vq);
       }
       cluster.sync();
       cur ^= 1;

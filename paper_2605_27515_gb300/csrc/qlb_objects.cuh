@@ -1,6 +1,7 @@
 // Object model behind the opaque C-ABI handles.
 #pragma once
 
+#include <atomic>
 #include <map>
 #include <memory>
 #include <string>
@@ -166,9 +167,17 @@ struct LaunchRec {
   const int* dims = nullptr;
 };
 
+// A number no other state of the process has had (group graphs are keyed by it:
+// a new state may reuse a destroyed one's address).
+inline unsigned long long next_state_uid() {
+  static std::atomic<unsigned long long> n{0};
+  return ++n;
+}
+
 }  // namespace qlb
 
 struct qlb_state {
+  const unsigned long long uid = qlb::next_state_uid();
   qlb_system* sys = nullptr;
   int L = 0;
   int prec = QLB_PREC_F64;

@@ -1461,7 +1461,8 @@ static qlb_status group_capture(GroupExec& gx, const std::vector<qlb_state*>& ms
   cudaGraphDestroy(gr);
   QLB_CUDA_TRY(e);
   gx.keys.resize(S);
-  gx.who.assign(ms.begin(), ms.end());
+  gx.who.resize(S);
+  for (int m = 0; m < S; m++) gx.who[m] = ms[m]->uid;
   for (int m = 0; m < S; m++) gx.keys[m] = ms[m]->plan_key;
   gx.launches = launches;
   return QLB_OK;
@@ -1471,7 +1472,7 @@ qlb_status group_run(GroupExec& gx, const std::vector<qlb_state*>& ms, cudaStrea
                      bool sync) {
   if (n <= 0 || ms.empty()) return QLB_OK;
   bool fresh = gx.graph && gx.keys.size() == ms.size() && gx.who.size() == ms.size();
-  for (size_t m = 0; fresh && m < ms.size(); m++) fresh = gx.who[m] == ms[m] && gx.keys[m] == ms[m]->plan_key;
+  for (size_t m = 0; fresh && m < ms.size(); m++) fresh = gx.who[m] == ms[m]->uid && gx.keys[m] == ms[m]->plan_key;
   qlb_status s;
   // the members' earlier work (their own streams) comes first
   for (qlb_state* st : ms) {

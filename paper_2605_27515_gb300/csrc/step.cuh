@@ -30,7 +30,7 @@ struct GroupExec {
   qlb_ctx* ctx = nullptr;
   cudaGraphExec_t graph = nullptr;
   std::vector<int> keys;   // members' plan keys at capture
-  std::vector<const qlb_state*> who;  // the members at capture
+  std::vector<unsigned long long> who;  // the members' uids at capture
   void* d_tab = nullptr;   // device table of the members' launch descriptors
   int launches = 0;        // kernel launches per captured step
   void release();
