@@ -600,6 +600,40 @@ def serving_summary(dev, n_requests, step_scale, precision, budget_gb=4.0):
     return out
 
 
+def run_serving_window(args):
+    """The serving configuration as stated: all 256 requests of the mix (Poisson
+    arrivals at 200/s, seed 20260527, their own step counts of 2000-20000, dt =
+    1e-3, chi caps 32/48/64, chi_mu <= 8) through the library's server for a fixed
+    wall window; reports the requests completed in the window with their p50/p99
+    latency and the steps the server enqueued per second (chunks still in flight
+    at the end of the window included)."""
+    import torch
+
+    from paper_2605_27515_gb300 import inputs, qlb, serving
+
+    torch.cuda.set_device(0)
+    budget_gb = 16.0
+    ctx = qlb.Ctx(device=0, precision=max(args.precision, 0), chi_max=64, chi_mu_max=8, stream_ordered=1)
+    reqs = inputs.serving_requests(n=256)
+    srv = qlb.Server(ctx, hbm_budget=int(budget_gb * (1 << 30)), max_live=64, chunk=100)
+    with ClockSampler(0) as clk:
+        jobs, used = serving.drive_window(srv, reqs, args.serving_window)
+        stats = srv.stats()
+    srv.close()
+    ctx.close()
+    out = serving.summarize_window(jobs, used, stats["steps"])
+    line = {"metric": METRIC, "value": out["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": stats["steps"],
+            "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": FORM_DTYPE[max(args.precision, 0)], "data": "synthetic",
+            "config": {"workload": "serving_window", "requests": 256, "arrivals": "Poisson 200/s, seed 20260527",
+                       "steps_per_request": "U{2000..20000}", "dt": 1e-3, "chi_max": "U{32,48,64}", "chi_mu_max": 8,
+                       "max_live": 64, "chunk": 100, "hbm_budget_bytes": int(budget_gb * (1 << 30)),
+                       "engine": "qlb_server (C-ABI), same-shape buckets stepped as groups"},
+            "serving": dict(out, peak_live=stats["peak_live"], peak_device_bytes=stats["peak_bytes"]),
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -612,11 +646,13 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--window2", type=int, default=200)
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "transmon", "cat_pair", "z_gate_sweep", "solvers"])
+                    choices=[WORKLOAD, "transmon", "cat_pair", "z_gate_sweep", "solvers", "serving_window"])
     ap.add_argument("--solver-n", type=int, nargs="+", default=[8, 16, 24, 32, 48, 64, 96, 128, 192, 256])
     ap.add_argument("--z-ra", type=int, nargs="+", default=[4, 5, 6])
     ap.add_argument("--z-dt", type=float, default=4e-3)
     ap.add_argument("--serving-step-scale", type=float, default=0.005)
+    ap.add_argument("--serving-window", type=float, default=60.0,
+                    help="--workload serving_window: seconds of wall time the full request mix runs")
     ap.add_argument("--mixed-gemm", type=int, default=1, choices=[0, 1, 2],
                     help="GEMMs of the mixed forms in double-float: 0 none, 1 all but the Grams, 2 all")
     args = ap.parse_args()
@@ -627,6 +663,8 @@ def main():
         run_z_gate_sweep(args)
     elif args.workload == "solvers":
         run_solver_sweep(args)
+    elif args.workload == "serving_window":
+        run_serving_window(args)
     elif args.workload != WORKLOAD:
         run_other_workload(args)
     else:

@@ -1,13 +1,14 @@
 """Serving workload driver over the library's continuous-batching server.
 
 The scheduling itself (admission by device-memory budget and live slots, chunked
-stepping of every live state on its own stream, completion, release) runs in
+stepping of the live states as same-shape groups, completion, release) runs in
 libqlb (qlb_server_*, csrc/server.cu).  This module only
   * turns a request of the serving mix (a single cat mode with its own alpha^2,
     Fock size, loss ratio, step count and bond caps) into the term lists of a
     qlb_request (argument marshalling),
   * submits the requests at their arrival times and polls for completions
-    (`drive`), and
+    (`drive`; `drive_window` runs the mix with its own step counts for a fixed
+    wall window and cancels what is left), and
   * summarises latencies (completion - arrival) and throughput.
 """
 from __future__ import annotations
@@ -88,6 +89,58 @@ def drive(server, requests, step_scale: float = 1.0, time_scale: float = 1.0, mi
         if open_jobs or nxt < len(jobs):
             sleep(poll_s)
     return jobs
+
+
+def drive_window(server, requests, window_s: float, poll_s: float = 0.0005, clock=time.perf_counter,
+                 sleep=time.sleep):
+    """The request mix as stated (every request with its own step count) for a fixed
+    wall window: submit each request at its arrival time, collect completions until
+    window_s has passed, then cancel what is still pending or running.  Returns the
+    jobs (done = 0 for the unfinished ones) and the window actually used."""
+    jobs = sorted((Job(req=r, arrival=r["arrival_s"], steps=int(r["steps"])) for r in requests),
+                  key=lambda j: j.arrival)
+    t0 = clock()
+    nxt = 0
+    open_jobs = []
+    while clock() - t0 < window_s:
+        now = clock() - t0
+        while nxt < len(jobs) and jobs[nxt].arrival <= now:
+            j = jobs[nxt]
+            q = cat_request(j.req)
+            j.ticket = server.submit(q["R"], q["H"], q["jumps"], q["vecs"], q["dt"], j.steps, q["obs"],
+                                     tol=q["tol"], chi_max=q["chi_max"], chi_mu_max=q["chi_mu_max"])
+            j.submitted = now
+            open_jobs.append(j)
+            nxt += 1
+        still = []
+        for j in open_jobs:
+            r = server.poll(j.ticket)
+            if r is None:
+                still.append(j)
+                continue
+            vals, times = r
+            j.done = clock() - t0
+            j.result = {"n": vals[0].real, "parity": vals[1].real}
+            j.server_times = times
+        open_jobs = still
+        sleep(poll_s)
+    used = clock() - t0
+    for j in open_jobs:
+        server.cancel(j.ticket)
+    return jobs[:nxt], used
+
+
+def summarize_window(jobs, window_s: float, steps_taken: int):
+    """Completed requests, their latencies, and the steps all requests took in the
+    window (finished or not) per second."""
+    done = [j for j in jobs if j.done > 0]
+    lat = np.array([j.done - j.arrival for j in done])
+    out = {"window_s": window_s, "submitted": len(jobs), "completed": len(done),
+           "steps_taken": int(steps_taken), "steps_per_s": steps_taken / window_s if window_s > 0 else None}
+    if len(done):
+        out.update({"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                    "completed_steps": int(sum(j.steps for j in done))})
+    return out
 
 
 def summarize(jobs, wall_s: float):

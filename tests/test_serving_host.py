@@ -68,3 +68,41 @@ def test_drive_submits_at_arrival_and_collects_everything():
         assert j.result["n"] == float(j.steps)  # the stand-in returns the step count
     s = serving.summarize(jobs, clk.t)
     assert s["requests"] == 12 and s["p99_latency_s"] >= s["p50_latency_s"] > 0
+
+
+class _SlowServer(_FakeServer):
+    """Finishes a request after `steps // 1000` polls and records cancellations."""
+
+    def __init__(self, clock):
+        super().__init__(clock)
+        self.cancelled = []
+
+    def submit(self, R, H, jumps, vecs, dt, steps, obs, tol=0.0, chi_max=0, chi_mu_max=0):
+        t = super().submit(R, H, jumps, vecs, dt, steps, obs, tol, chi_max, chi_mu_max)
+        self.jobs[t][0] = steps // 1000
+        return t
+
+    def cancel(self, t):
+        self.cancelled.append(t)
+
+
+def test_drive_window_stops_at_the_window_and_cancels_the_rest():
+    """The stated mix (own step counts) for a fixed window: requests arriving after
+    the window are never submitted, unfinished ones are cancelled, and the summary
+    counts only completed requests for latency."""
+    reqs = inputs.serving_requests(n=40, seed=4)
+    clk = _Clock()
+    srv = _SlowServer(clk)
+    window = reqs[20]["arrival_s"] + 0.01  # about half of the arrivals fall inside
+    jobs, used = serving.drive_window(srv, reqs, window, poll_s=2e-3, clock=clk, sleep=clk.sleep)
+    assert used >= window
+    assert len(jobs) == len(srv.log) and 21 <= len(jobs) < 40
+    assert all(j.steps == j.req["steps"] for j in jobs)  # not scaled
+    done = [j for j in jobs if j.done > 0]
+    assert sorted(srv.cancelled) == sorted(j.ticket for j in jobs if j.done == 0)
+    assert all(j.result["n"] == float(j.steps) for j in done)
+    s = serving.summarize_window(jobs, used, steps_taken=12345)
+    assert s["submitted"] == len(jobs) and s["completed"] == len(done)
+    assert s["steps_per_s"] == 12345 / used
+    if done:
+        assert s["p99_latency_s"] >= s["p50_latency_s"] >= 0
