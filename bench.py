@@ -616,11 +616,13 @@ def run_serving_window(args):
     ctx = qlb.Ctx(device=0, precision=max(args.precision, 0), chi_max=64, chi_mu_max=8, stream_ordered=1)
     reqs = inputs.serving_requests(n=256)
     srv = qlb.Server(ctx, hbm_budget=int(budget_gb * (1 << 30)), max_live=64, chunk=100)
-    with ClockSampler(0) as clk:
-        jobs, used = serving.drive_window(srv, reqs, args.serving_window)
-        stats = srv.stats()
-    srv.close()
-    ctx.close()
+    try:
+        with ClockSampler(0) as clk:
+            jobs, used = serving.drive_window(srv, reqs, args.serving_window)
+            stats = srv.stats()
+    finally:
+        srv.close()
+        ctx.close()
     out = serving.summarize_window(jobs, used, stats["steps"])
     line = {"metric": METRIC, "value": out["steps_per_s"], "unit": "steps/s", "n_gpus": 1, "steps": stats["steps"],
             "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -528,7 +528,11 @@ qlb_status tt_svd(qlb_ctx* ctx, zd* T, int L, int P, double tol, int cap, std::v
     qlb_status st = svd_osj(ctx, cur, m, (int)n, tol, cap, &U, 0, &Rr, 0, &k, 60);
     dev_free(ctx, cur);
     if (st) {
-      for (auto p : cores) dev_free(ctx, p);
+      // the caller's vector must not keep the freed cores (its owner frees them again)
+      for (auto& p : cores) {
+        dev_free(ctx, p);
+        p = nullptr;
+      }
       return st;
     }
     // U is m x m storage with k columns used: compact it into the core [r][P][k]

@@ -722,7 +722,9 @@ qlb_status plan_buffers(qlb_state* st, const Kraus& K) {
   n_eig = std::max(n_eig, c.zcap[0]);
   nT = std::max({nT, (size_t)c.zcap[0] * c.dcap[0], (size_t)c.dcap[0] * 2 * c.dcap[1], (size_t)c.zcap[0] * 2 * c.dcap[1]});
   if (n_eig > 512) {
-    set_error("a truncation would need an eigen-solve of size " + std::to_string(n_eig) + " (> 512)");
+    std::string dims;
+    for (int v : cur) dims += " " + std::to_string(v);
+    set_error("a truncation would need an eigen-solve of size " + std::to_string(n_eig) + " (> 512); bond dims" + dims);
     return QLB_EINVAL;
   }
   if ((s = realloc_buf(ctx, &st->X, &st->nX, nX))) return s;

@@ -50,6 +50,7 @@ class Job:
     done: float = 0.0
     result: dict = field(default_factory=dict)
     server_times: tuple = ()
+    failed: str = ""
 
 
 def drive(server, requests, step_scale: float = 1.0, time_scale: float = 1.0, min_steps: int = 10,
@@ -114,7 +115,11 @@ def drive_window(server, requests, window_s: float, poll_s: float = 0.0005, cloc
             nxt += 1
         still = []
         for j in open_jobs:
-            r = server.poll(j.ticket)
+            try:
+                r = server.poll(j.ticket)
+            except Q.QlbError as e:  # a failed request is reported, not fatal to the window
+                j.failed = str(e)
+                continue
             if r is None:
                 still.append(j)
                 continue
@@ -135,8 +140,11 @@ def summarize_window(jobs, window_s: float, steps_taken: int):
     window (finished or not) per second."""
     done = [j for j in jobs if j.done > 0]
     lat = np.array([j.done - j.arrival for j in done])
-    out = {"window_s": window_s, "submitted": len(jobs), "completed": len(done),
+    failed = [j for j in jobs if j.failed]
+    out = {"window_s": window_s, "submitted": len(jobs), "completed": len(done), "failed": len(failed),
            "steps_taken": int(steps_taken), "steps_per_s": steps_taken / window_s if window_s > 0 else None}
+    if failed:
+        out["first_failure"] = failed[0].failed
     if len(done):
         out.update({"p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                     "completed_steps": int(sum(j.steps for j in done))})

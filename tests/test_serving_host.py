@@ -106,3 +106,23 @@ def test_drive_window_stops_at_the_window_and_cancels_the_rest():
     assert s["steps_per_s"] == 12345 / used
     if done:
         assert s["p99_latency_s"] >= s["p50_latency_s"] >= 0
+
+
+class _FailingServer(_SlowServer):
+    """Request 2 fails: its poll raises the library's error."""
+
+    def poll(self, t):
+        if t == 2:
+            raise Q.QlbError(Q.EINVAL, "request failed")
+        return super().poll(t)
+
+
+def test_drive_window_reports_a_failed_request():
+    reqs = inputs.serving_requests(n=10, seed=5)
+    clk = _Clock()
+    srv = _FailingServer(clk)
+    jobs, used = serving.drive_window(srv, reqs, reqs[-1]["arrival_s"] + 0.01, poll_s=2e-3, clock=clk,
+                                      sleep=clk.sleep)
+    s = serving.summarize_window(jobs, used, steps_taken=1)
+    assert s["failed"] == 1 and "request failed" in s["first_failure"]
+    assert 2 not in srv.cancelled  # a failed request is not cancelled again
