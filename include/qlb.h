@@ -282,8 +282,11 @@ qlb_status qlb_state_import(qlb_state* st, const void* in, size_t n_bytes);
  * CTA, cluster or GEMM grid slice per member, blockIdx.y = member), captured as
  * one CUDA graph on the group's own stream, so n_states states cost one chain of
  * launches.  A member's numbers are the ones its own qlb_step computes: the same
- * kernels, shapes, K splits and reduction orders (results equal bit for bit when
- * the members share one planned shape).
+ * kernels, shapes, K splits and reduction orders, bit for bit when the members
+ * share one planned shape.  When planned sizes differ, an eigen-solve may run on
+ * the kernel the largest co-member's size needs (the same rotations, thresholds
+ * and truncation rule: results agree to rounding).  The per-class timings of
+ * qlb_profile_* do not cover group steps; the solver counters do.
  *
  * The members must belong to ctx, be distinct, and step the same launch sequence:
  * the same number of sites, the same precision form and Kraus scheme (their mode
